@@ -1,0 +1,114 @@
+/*
+ * oracle.h -- plain, slow FP64 CPU oracle for the MLMC boundary-layer
+ * dispersion path of Katsiolides, Mueller, Scheichl, Shardlow, Giles and
+ * Thomson, "Multilevel Monte Carlo and improved timestepping methods in
+ * atmospheric dispersion modelling" (arXiv 1612.07717).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library
+ * and its Python binding) includes, links or calls this code; only the tests,
+ * the smoke check and the CPU-baseline leg of the benchmark do.  It shares no
+ * code, header, table or constant with the CUDA path: the Philox generator
+ * and the normal map are implemented here a second time from their published
+ * definitions.
+ *
+ * Every quantity is double precision.  Each function names the passage of
+ * the paper it restates.
+ */
+#ifndef MLMC_ORACLE_H
+#define MLMC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_SE = 0, ORC_GL = 1, ORC_BAOAB = 2 };
+/* uniform map applied to one 32-bit Philox word */
+enum { ORC_U23 = 0,   /* u = (floor(x / 2^9) + 1/2) * 2^-23 : the FP32 kernel's map */
+       ORC_U32 = 1 }; /* u = (x + 1/2) * 2^-32                : the FP64 kernel's map */
+
+typedef struct {
+  double u_star;        /* friction velocity u* [m/s]                              */
+  double f_coriolis;    /* Coriolis parameter f [1/s]                              */
+  double H;             /* boundary-layer depth [m]; <= 0 means 0.3 u* / f           */
+  double kappa_sigma;   /* 1.3  (Eq. profiles)                                     */
+  double kappa_tau;     /* 0.5  (Eq. profiles)                                     */
+  double c_f;           /* tau divided by (1 + c_f f z / u*); 0 gives the paper's tau */
+  double eps_reg_frac;  /* regularisation height eps_reg as a fraction of H        */
+  double z0, w0;        /* release height [m], fixed release velocity [m/s]        */
+  double T;             /* travel time [s]                                         */
+  double qoi_threshold; /* indicator QoI: 1[z(T) < qoi_threshold] [m]              */
+  int32_t w0_mode;      /* 0 fixed w0; 1 w0 ~ N(0, sigma_w(z0)^2); 2 well mixed    */
+  int32_t M0;           /* timesteps on level 0; level l uses M0 * 2^l             */
+  int32_t level_min;    /* coarsest level of the hierarchy (plain MC on it)         */
+  int32_t L_max;        /* finest level the adaptive driver may add                 */
+  int32_t coupling;     /* 0 reflection-aware coupling; 1 naive (all S = 1)         */
+  int32_t drift_outside;/* 0 d(sigma_w^2)/dz = 0 outside the band; 1 frozen value   */
+  int32_t n_init;       /* initial samples on a new level (adaptive driver)         */
+  int32_t uniform_map;  /* ORC_U23 or ORC_U32                                       */
+  uint32_t stream_id;   /* Philox counter word 3 (one stream per query)             */
+  int32_t pad_;
+} orc_params;
+
+typedef struct {
+  double zf, wf, zc, wc; /* final states of the fine and coarse path          */
+  int32_t nonfinite;     /* 1 if either path left |z| <= 1e3 H or became NaN  */
+  int32_t refl_f, refl_c;/* number of reflections on each path                */
+  int32_t pad_;
+} orc_path_out;
+
+/* per QoI q (0: z(T), 1: 1[z(T) < threshold]) the six sums
+ * sum[q] = { sum Y, sum Y^2, sum P_f, sum P_f^2, sum P_c, sum P_c^2 } */
+typedef struct {
+  uint64_t n;           /* finite paths that entered the sums  */
+  uint64_t path_steps;  /* integrator steps executed (fine + coarse) */
+  uint64_t n_nonfinite; /* paths excluded as diverged          */
+  uint64_t pad_;
+  double sum[2][6];
+} orc_level_sums_t;
+
+#define ORC_MAX_LEVELS 32
+typedef struct {
+  double estimate[2];        /* MLMC estimate of E[P] per QoI                  */
+  double est_variance[2];    /* sum_l V_l / N_l per QoI                          */
+  int32_t L;                 /* finest level used                                */
+  int32_t converged;         /* 1 if the bias test passed before L_max           */
+  uint64_t N[ORC_MAX_LEVELS];     /* samples per level (index = level)           */
+  double V[ORC_MAX_LEVELS];       /* sample variance of Y_l (QoI 0)              */
+  double mean_y[ORC_MAX_LEVELS];  /* mean of Y_l (QoI 0)                         */
+  uint64_t total_path_steps;
+  uint64_t n_nonfinite;
+} orc_result_t;
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* The four standard normals of fine steps 4k..4k+3 of path i on level l. */
+void orc_normals4(const orc_params* p, int level, uint64_t i, uint32_t block,
+                  uint64_t seed, double xi[4]);
+
+/* sigma_w, sigma_w^2, d(sigma_w^2)/dz, lambda, sigma at height z. */
+void orc_coefficients(const orc_params* p, double z, double out[5]);
+
+/* Fill defaults that depend on others (H from u*, f).  Returns 0 or -1. */
+int orc_normalise(orc_params* p);
+
+/* One coupled path pair of level `level` (fine only when level ==
+ * level_min).  trace_f (3 * (M+1) doubles: z, w, S per fine time point) and
+ * trace_c (3 * (M/2+1)) are optional.  Returns 0, or -1 on bad arguments. */
+int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
+             orc_path_out* out, double* trace_f, double* trace_c);
+
+/* Level sums over paths [offset, offset + N).  threads <= 0 uses 1.  The
+ * result does not depend on the thread count. */
+int orc_level_sums(const orc_params* p, int integ, int level, uint64_t N,
+                   uint64_t offset, uint64_t seed, int threads, orc_level_sums_t* out);
+
+/* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Giles 2008, Section 5). */
+int orc_estimate(const orc_params* p, int integ, double eps, uint64_t seed,
+                 int threads, orc_result_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
