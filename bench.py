@@ -1,0 +1,286 @@
+"""Benchmark of the MLMC dispersion hot path on GB300.
+
+One step = one pass of the whole hot path over the batched multi-level
+workload: all MLMC levels l = 0..12 of the 600 m boundary layer with N_l =
+1e9 * 10^(-l/2) path pairs (1e9 on level 0 down to 1e3 on level 12), BAOAB
+integrator, FP32 paths, FP64 compensated sums, in ONE persistent launch,
+followed by the fixed-order per-level reduction -- about 2.85e10 path-steps.
+
+Prints one JSON line (see the keys below).  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+INTEGRATOR = 2          # BAOAB
+LEVELS = 13
+N0 = 1e9
+# FP32 arithmetic per path-step of a coupled BAOAB level, counted from the
+# step formulas as the kernel evaluates them (FMA = 2, other arithmetic,
+# square root, reciprocal, exp, log, sin, cos = 1 each); the derivation is
+# in the design doc.  Per coupled pair of fine steps: 3 BAOAB steps of 71, the
+# coarse coupling 9, two Box-Muller normals 12 -> 234 / 3 path-steps.
+FLOPS_PER_PATH_STEP = 78.0
+ORACLE_SAMPLE_SCALE = 2e-3
+
+
+def workload():
+    from paper_1612_07717_gb300 import workloads as W
+    return W.schedule_c4(levels=LEVELS, n0=N0)
+
+
+def path_steps_of(sched, M0=8):
+    tot = 0
+    for l, n in sched:
+        M = M0 << l
+        tot += n * (M + M // 2 if l > 0 else M)
+    return tot
+
+
+def sample_clocks(stop_file, out_file):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+           "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-i", "0",
+           "-lms", "100"]
+    try:
+        return subprocess.Popen(cmd, stdout=open(out_file, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def parse_clocks(path):
+    sm, mx, reasons = [], [], set()
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+    except FileNotFoundError:
+        pass
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+            "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def fp32_peak_probe(torch, lib_probe=None):
+    """Measured FP32 FMA rate (FLOP/s) of this GPU from the library's probe kernel."""
+    import ctypes as C
+    import paper_1612_07717_gb300 as G
+    L = G.lib()
+    if not hasattr(L, "mlmc_fp32_peak_probe"):
+        return None
+    L.mlmc_fp32_peak_probe.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+    buf = torch.empty(1 << 20, dtype=torch.float32, device="cuda")
+    out = C.c_double()
+    best = 0.0
+    for _ in range(3):
+        rc = L.mlmc_fp32_peak_probe(4096, C.c_void_p(buf.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                    C.byref(out))
+        if rc == 0:
+            best = max(best, out.value)
+    return best or None
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a bounded sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1612_07717_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    po = O.make_params(W.bl600(INTEGRATOR), uniform_map=O.U23)
+    sched = [(l, max(1, int(round(n * ORACLE_SAMPLE_SCALE)))) for l, n in workload()]
+    steps = path_steps_of(sched)
+
+    def one(seed):
+        t = time.perf_counter()
+        for l, n in sched:
+            O.level_sums(po, INTEGRATOR, l, n, 0, seed, threads=threads)
+        return time.perf_counter() - t
+
+    for w in range(args.warmup):
+        one(100 + w)
+    ts = [one(1 + k) for k in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts)
+    value = steps / (ms / 1e3)
+    sample = ("levels 0..12 of the batched BAOAB workload with N_l scaled by %g (%d path-steps "
+              "per step)" % (ORACLE_SAMPLE_SCALE, steps))
+    line = {
+        "impl": "reference",
+        "metric": "path-steps/s", "value": value, "unit": "path-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "batched-multilevel-l0-12-bl600-baoab (oracle sample)",
+                   "sample_scale": ORACLE_SAMPLE_SCALE, "path_steps_per_step": steps},
+        "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline_sample():
+    """Oracle throughput on host cores for the cpu_baseline key (about 10 s)."""
+    from oracle import oracle as O
+    from paper_1612_07717_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    po = O.make_params(W.bl600(INTEGRATOR), uniform_map=O.U23)
+    sched = [(l, max(1, int(round(n * ORACLE_SAMPLE_SCALE)))) for l, n in workload()]
+    steps = path_steps_of(sched)
+    t = time.perf_counter()
+    for l, n in sched:
+        O.level_sums(po, INTEGRATOR, l, n, 0, 1, threads=threads)
+    dt = time.perf_counter() - t
+    return {"value": steps / dt, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+            "sample": "levels 0..12 of the same workload with N_l x %g (%d path-steps, %.1f s)"
+                      % (ORACLE_SAMPLE_SCALE, steps, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n0", type=float, default=N0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import ctypes as C
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_07717_gb300 as G
+    from paper_1612_07717_gb300 import workloads as W
+
+    # each rank takes its own slice of every level's path range (weak scaling:
+    # the per-GPU work is the full schedule; ranks use disjoint path indices)
+    sched = [(l, int(round(n * args.n0 / N0))) for l, n in workload()]
+    reqs = [(l, rank * n, n) for l, n in sched]
+    params = G.make_params(W.bl600(INTEGRATOR), precision=G.FP32)
+    steps_per_step = path_steps_of(sched)
+    launch = G.MultilevelLaunch(reqs, INTEGRATOR, params, seed=1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    for w in range(args.warmup):
+        launch.run(stream)
+    torch.cuda.synchronize()
+
+    clk_file = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_file), exist_ok=True)
+    sampler = sample_clocks(None, clk_file) if rank == 0 else None
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for k in range(args.steps):
+        flush.zero_()                              # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launch.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    ms = sum(times) / len(times)
+    t_max = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    res = launch.results()
+    assert all(r["n"] == c for r, (_, _, c) in zip(res, launch.requests)), "lost paths"
+
+    # end to end through the public C ABI with host requests and host results
+    e2e_times = []
+    reqs_host = list(launch.requests)
+    for k in range(max(2, args.steps // 2)):
+        t = time.perf_counter()
+        G.multilevel_sums(reqs_host, INTEGRATOR, params, 1, workspace=launch.ws)
+        e2e_times.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e_times)
+
+    clocks = parse_clocks(clk_file) if rank == 0 else None
+    peak_probe = fp32_peak_probe(torch)
+    value = world * steps_per_step / (ms / 1e3)
+    out = None
+    if rank == 0:
+        sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+        info = G.device_info()
+        derived_peak = info["sms"] * 128 * 2 * sm_mhz * 1e6
+        peak = peak_probe or derived_peak
+        achieved = FLOPS_PER_PATH_STEP * steps_per_step / (ms / 1e3)
+        n_req = len(reqs_host)
+        out = {
+            "metric": "path-steps/s", "value": value, "unit": "path-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched-multilevel-l0-12-bl600-baoab",
+                       "levels": "0..12", "N_l": "1e9*10^(-l/2) (level 0: %d, level 12: %d)"
+                       % (sched[0][1], sched[-1][1]),
+                       "path_steps_per_step": steps_per_step, "integrator": "BAOAB",
+                       "paths": "fp32", "sums": "fp64 Kahan",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "measured FFMA probe" if peak_probe else
+                         "derived SMs*128*2*clock at %.0f MHz" % sm_mhz,
+                         "flops_per_path_step": FLOPS_PER_PATH_STEP},
+            "e2e": {"value": world * steps_per_step / e2e_s, "unit": "path-steps/s",
+                    "h2d_bytes_per_step": C.sizeof(G.LevelRequest) * n_req + C.sizeof(G.Params),
+                    "d2h_bytes_per_step": C.sizeof(G.LevelResult) * n_req},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

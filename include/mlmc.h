@@ -1,0 +1,220 @@
+/*
+ * mlmc.h -- C ABI of the GB300 (sm_103a) library for multilevel Monte Carlo
+ * estimation of particle dispersion in a 1-D atmospheric boundary layer, after
+ * Katsiolides, Mueller, Scheichl, Shardlow, Giles and Thomson, "Multilevel
+ * Monte Carlo and improved timestepping methods in atmospheric dispersion
+ * modelling" (arXiv 1612.07717).
+ *
+ * The problem (Section 2, Eq. generalised): a particle at height z with
+ * vertical velocity w follows
+ *     dw = [-w / tau(z) + 1/2 (1 + w^2 / sigma_w^2) d sigma_w^2/dz] dt
+ *          + sqrt(2 sigma_w^2 / tau) dW,        dz = w dt,
+ * reflected elastically at z = 0 and z = H (Section 4).  The library
+ * estimates E[phi(z(T))] for phi(z) = z and phi(z) = 1[z < threshold] with
+ * plain Monte Carlo (Eq. StMCestimator) or multilevel Monte Carlo (Eqs.
+ * telescoping_sum, mlmcestimator, Yhatell), using the symplectic Euler,
+ * geometric Langevin or BAOAB integrator (Section 3.1) and the
+ * reflection-aware coupling of fine and coarse paths (Eqs.
+ * euler_coupled_treatment and splitting_coupled_treatment).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers; all others are host pointers.
+ *  - The caller owns all memory.  The library never allocates device memory:
+ *    device scratch is the caller's `workspace` of `ws_bytes` bytes, sized by
+ *    mlmc_workspace_bytes().  Host output structs are written in place.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels are
+ *    launched on it.  Entry points that return results in a host struct
+ *    synchronise that stream before returning; *_async entry points do not.
+ *  - Return value: MLMC_OK (0) or a negative mlmc_status.  On an error no
+ *    output is valid unless stated.  mlmc_strerror() names the code.
+ *  - Random numbers: Philox4x32-10 with key = seed and counter =
+ *    (step_block, path_lo, path_hi ^ (level << 24), stream_id); fine step n
+ *    of a path uses word n mod 4 of block n / 4, Box-Muller on word pairs.
+ *    A path's samples therefore depend only on (seed, stream_id, level, path
+ *    index): splitting [0, N) into calls over [0, a) and [a, N) with
+ *    path_offset gives the same paths.
+ */
+#ifndef MLMC_GB300_H
+#define MLMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+typedef enum {
+  MLMC_OK = 0,
+  MLMC_EINVAL = -1,      /* invalid argument or parameter                      */
+  MLMC_EWORKSPACE = -2,  /* workspace NULL, misaligned or too small             */
+  MLMC_ECUDA = -3,       /* a CUDA call failed (launch, copy, sync)             */
+  MLMC_ENONFINITE = -4,  /* some paths diverged; they are excluded and counted,
+                            every other output is valid                        */
+  MLMC_ETIMEOUT = -5,    /* a device-side work loop hit its iteration limit    */
+  MLMC_EUNSTABLE = -6,   /* symplectic Euler requested with h lambda_max >= 2   */
+  MLMC_ENOTCONV = -7,    /* adaptive driver reached L_max before its bias test
+                            passed; the estimate is still returned              */
+  MLMC_ENODEV = -8       /* no CUDA device or unsupported architecture          */
+} mlmc_status;
+
+typedef enum { MLMC_SE = 0, MLMC_GL = 1, MLMC_BAOAB = 2 } mlmc_integrator;
+typedef enum { MLMC_FP32 = 0, MLMC_FP64 = 1 } mlmc_precision;
+
+/* ------------------------------------------------------------- parameters */
+/* Scenario and hierarchy.  Profiles (Eq. profiles, Eq. regularisation):
+ *   z_c     = clamp(z, eps_reg, H - eps_reg),  eps_reg = eps_reg_frac * H
+ *   sigma_w = kappa_sigma u* (1 - z_c / H)^(3/4)
+ *   tau     = kappa_tau z_c / sigma_w / (1 + c_f f z_c / u*)
+ *   d sigma_w^2 / dz of the regularised profile (0 outside the band).
+ * Level l integrates M0 * 2^l steps of h = T / (M0 2^l); the coarsest level
+ * level_min is plain Monte Carlo, finer levels are coupled pairs. */
+typedef struct mlmc_params {
+  double u_star;        /* friction velocity u* [m/s], > 0                    */
+  double f_coriolis;    /* Coriolis parameter f [1/s], >= 0                    */
+  double H;             /* boundary-layer depth [m]; <= 0 selects 0.3 u* / f   */
+  double kappa_sigma;   /* 1.3                                                  */
+  double kappa_tau;     /* 0.5                                                  */
+  double c_f;           /* Coriolis factor on tau (15; 0 = the paper's tau)     */
+  double eps_reg_frac;  /* eps_reg / H, in (0, 0.5]                             */
+  double z0;            /* release height [m] (w0_mode 0 and 1)                 */
+  double w0;            /* release velocity [m/s] (w0_mode 0)                   */
+  double T;             /* travel time [s], > 0                                 */
+  double qoi_threshold; /* indicator QoI 1[z(T) < qoi_threshold] [m]            */
+  int32_t w0_mode;      /* 0 fixed (z0, w0); 1 w0 ~ N(0, sigma_w(z0)^2);
+                           2 well mixed z0 ~ U(0, H), w0 ~ N(0, sigma_w(z0)^2)  */
+  int32_t M0;           /* steps on level 0, >= 1                                */
+  int32_t level_min;    /* coarsest level (plain Monte Carlo on it)              */
+  int32_t L_max;        /* finest level the adaptive driver may use, < 32        */
+  int32_t coupling;     /* 0 reflection-aware (paper); 1 naive S = 1 (for study) */
+  int32_t drift_outside;/* 0 d sigma_w^2/dz = 0 outside the band; 1 frozen value */
+  int32_t n_init;       /* samples on a newly added level (adaptive driver)      */
+  int32_t precision;    /* mlmc_precision of the path arithmetic                 */
+  uint32_t stream_id;   /* Philox counter word 3: one random stream per query    */
+  int32_t allow_unstable; /* 1: run SE levels with h lambda_max >= 2 anyway      */
+} mlmc_params;
+
+/* Fill *p with the 600 m neutral boundary-layer scenario: u* = 0.2, f = 1e-4,
+ * H = 600, kappa_sigma = 1.3, kappa_tau = 0.5, c_f = 15, eps_reg = 1e-3 H,
+ * z0 = 0.1 H with w0 ~ N(0, sigma_w(z0)^2), T = 600 s, M0 = 8, levels 0..10,
+ * threshold 0.1 H, FP32 paths.  Returns MLMC_OK. */
+int mlmc_params_default(mlmc_params* p);
+
+/* ---------------------------------------------------------------- results */
+/* Per-level sums (Eq. Yhatell): for QoI q (0: z(T), 1: 1[z(T) < threshold])
+ * sum[q] = { sum Y, sum Y^2, sum P_f, sum P_f^2, sum P_c, sum P_c^2 } with
+ * Y = P_f - P_c (Y = P_f and P_c = 0 on level_min).  FP64, Kahan-compensated
+ * within thread blocks and reduced across blocks in a fixed order. */
+typedef struct mlmc_level_result {
+  uint64_t n;           /* finite path pairs in the sums                        */
+  uint64_t path_steps;  /* integrator steps executed (fine + coarse), all pairs */
+  uint64_t n_nonfinite; /* pairs excluded because a path diverged               */
+  uint64_t reserved;
+  double sum[2][6];
+} mlmc_level_result;
+
+#define MLMC_MAX_LEVELS 32
+typedef struct mlmc_result {
+  double estimate[2];            /* MLMC estimate of E[P] per QoI              */
+  double est_variance[2];        /* sum_l V_l / N_l per QoI                     */
+  int32_t L;                     /* finest level used                           */
+  int32_t converged;             /* 1 if the bias test passed                   */
+  uint64_t N[MLMC_MAX_LEVELS];   /* samples per level (index = level)           */
+  double V[MLMC_MAX_LEVELS];     /* sample variance of Y_l, QoI 0               */
+  double mean_y[MLMC_MAX_LEVELS];/* sample mean of Y_l, QoI 0                   */
+  uint64_t total_path_steps;
+  uint64_t n_nonfinite;
+  double seconds;                /* wall time of the call                       */
+} mlmc_result;
+
+/* A batch entry for the multi-level launch: `count` pairs of `level` with
+ * global path indices [first, first + count). */
+typedef struct mlmc_level_request {
+  int32_t level;
+  int32_t reserved;
+  uint64_t first;
+  uint64_t count;
+} mlmc_level_request;
+
+/* --------------------------------------------------------------- queries */
+const char* mlmc_strerror(int code);
+
+/* Library and device facts: out[0] = SM count, out[1] = compute capability
+ * (major * 10 + minor), out[2] = library version.  Returns MLMC_ENODEV if no
+ * device is visible. */
+int mlmc_device_info(int32_t out[3]);
+
+/* Bytes of device workspace that every entry point below needs for a batch
+ * of up to `max_requests` level requests (1 for single-level calls).  The
+ * workspace must be 256-byte aligned.  Pure host computation. */
+size_t mlmc_workspace_bytes(const mlmc_params* p, int max_requests);
+
+/* ------------------------------------------------------------ estimation */
+/* Sums of N coupled pairs of `level` (plain paths on level_min), paths
+ * [path_offset, path_offset + N); Section 3.2, Eq. (Yhatell).  Launches the
+ * coupled-level kernel and the fixed-order reduction on `stream`, copies the
+ * sums into *out and synchronises the stream.  Returns MLMC_ENONFINITE (with
+ * valid *out) if any pair diverged, MLMC_EUNSTABLE for an unstable SE level
+ * unless p->allow_unstable. */
+int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
+                    uint64_t seed, uint64_t path_offset, void* workspace, size_t ws_bytes,
+                    void* stream, mlmc_level_result* out);
+
+/* As mlmc_level_sums, for many levels in ONE persistent launch: blocks take
+ * fixed-size work items (largest per-path cost first) from an atomic queue;
+ * each item's block partial goes to its own slot and the slots of a request
+ * are reduced in item order, so the sums do not depend on scheduling.
+ * d_out: device array of n_req results.  No synchronisation. */
+int mlmc_multilevel_sums_async(const mlmc_level_request* reqs, int n_req, int integrator,
+                               const mlmc_params* p, uint64_t seed, void* workspace,
+                               size_t ws_bytes, void* stream, mlmc_level_result* d_out);
+
+/* Same, with host requests and host results (copies in, launch, copy out,
+ * synchronise): the end-to-end form of the batched launch. */
+int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrator,
+                         const mlmc_params* p, uint64_t seed, void* workspace,
+                         size_t ws_bytes, void* stream, mlmc_level_result* out);
+
+/* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Section 3.2 and the
+ * sample-size rule of Giles 2008 the paper adopts in Section 5): levels are
+ * added from level_min, N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k
+ * C_k)), converged when max(|Yhat_{L-1}| / 2, |Yhat_L|) < eps / sqrt(2).
+ * Host-driven loop of mlmc_level_sums calls on `stream`. */
+int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                  void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
+
+/* Plain Monte Carlo (Eq. StMCestimator) at `level`'s timestep to RMSE eps:
+ * n_pilot paths estimate Var[P], then N = ceil(2 Var / eps^2) in total. */
+int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator,
+                       const mlmc_params* p, uint64_t seed, void* workspace,
+                       size_t ws_bytes, void* stream, mlmc_result* out);
+
+/* ---------------------------------------------------------- path outputs */
+/* Final states of N pairs of `level` into d_states (N x 4 values of the path
+ * precision: z_f, w_f, z_c, w_c; coarse entries 0 on level_min) and
+ * d_flags (N int32: bit 0 diverged).  No synchronisation. */
+int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                           uint64_t seed, uint64_t path_offset, void* d_states,
+                           int32_t* d_flags, void* stream);
+
+/* Full trajectories of N pairs (meant for small N): d_trace_f gets N x (M+1)
+ * x 3 values (z, w, S per fine time point), d_trace_c N x (M/2+1) x 3 (may be
+ * NULL on level_min).  No synchronisation. */
+int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                          uint64_t seed, uint64_t path_offset, void* d_trace_f,
+                          void* d_trace_c, void* stream);
+
+/* ------------------------------------------------------------ measurement */
+/* The paper has no counterpart: this measures the roofline denominator of
+ * the path kernels.  Runs a kernel of independent FP32 FMA chains (8 per
+ * thread, `iters` iterations, every SM fully occupied) on `stream`, times it
+ * with CUDA events and writes the achieved FP32 rate in FLOP/s (FMA = 2) to
+ * *flops_per_s.  d_scratch: at least 4 MB of device memory that receives
+ * the chain results.  Synchronises the stream. */
+int mlmc_fp32_peak_probe(int iters, void* d_scratch, void* stream, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_GB300_H */

@@ -1,0 +1,285 @@
+"""GB300 (sm_103a) multilevel Monte Carlo for 1-D boundary-layer dispersion.
+
+Thin ctypes binding over the C ABI of ``libmlmc.so`` (declared in
+``include/mlmc.h``): argument marshalling only; every step of the path runs
+in the library's CUDA kernels.  PyTorch supplies device memory (the
+workspace and output tensors) and streams.  Importing the package does not
+load the library; the first call does, and it raises if the library has not
+been built -- there is no CPU fallback.
+
+Method: Katsiolides, Mueller, Scheichl, Shardlow, Giles, Thomson, "Multilevel
+Monte Carlo and improved timestepping methods in atmospheric dispersion
+modelling", arXiv 1612.07717.
+"""
+import ctypes as C
+import os
+
+from . import workloads  # noqa: F401  (inputs only; no library load)
+
+SE, GL, BAOAB = 0, 1, 2
+FP32, FP64 = 0, 1
+MAX_LEVELS = 32
+
+OK, EINVAL, EWORKSPACE, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTCONV, ENODEV = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmlmc.so")
+
+
+class Params(C.Structure):
+    """mirror of ``mlmc_params`` (include/mlmc.h)"""
+    _fields_ = [
+        ("u_star", C.c_double), ("f_coriolis", C.c_double), ("H", C.c_double),
+        ("kappa_sigma", C.c_double), ("kappa_tau", C.c_double), ("c_f", C.c_double),
+        ("eps_reg_frac", C.c_double), ("z0", C.c_double), ("w0", C.c_double),
+        ("T", C.c_double), ("qoi_threshold", C.c_double),
+        ("w0_mode", C.c_int32), ("M0", C.c_int32), ("level_min", C.c_int32),
+        ("L_max", C.c_int32), ("coupling", C.c_int32), ("drift_outside", C.c_int32),
+        ("n_init", C.c_int32), ("precision", C.c_int32), ("stream_id", C.c_uint32),
+        ("allow_unstable", C.c_int32),
+    ]
+
+
+class LevelResult(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("path_steps", C.c_uint64), ("n_nonfinite", C.c_uint64),
+                ("reserved", C.c_uint64), ("sum", (C.c_double * 6) * 2)]
+
+
+class Result(C.Structure):
+    _fields_ = [("estimate", C.c_double * 2), ("est_variance", C.c_double * 2),
+                ("L", C.c_int32), ("converged", C.c_int32),
+                ("N", C.c_uint64 * MAX_LEVELS), ("V", C.c_double * MAX_LEVELS),
+                ("mean_y", C.c_double * MAX_LEVELS), ("total_path_steps", C.c_uint64),
+                ("n_nonfinite", C.c_uint64), ("seconds", C.c_double)]
+
+
+class LevelRequest(C.Structure):
+    _fields_ = [("level", C.c_int32), ("reserved", C.c_int32), ("first", C.c_uint64),
+                ("count", C.c_uint64)]
+
+
+assert C.sizeof(Params) == 128 and C.sizeof(LevelResult) == 128
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmlmc.so not built: run paper_1612_07717_gb300.build.build() "
+                               "(expected at %s)" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int
+        L.mlmc_strerror.restype = C.c_char_p
+        L.mlmc_strerror.argtypes = [i32]
+        L.mlmc_params_default.argtypes = [C.POINTER(Params)]
+        L.mlmc_device_info.argtypes = [C.POINTER(C.c_int32)]
+        L.mlmc_workspace_bytes.restype = C.c_size_t
+        L.mlmc_workspace_bytes.argtypes = [C.POINTER(Params), i32]
+        L.mlmc_level_sums.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, C.c_size_t,
+                                      vp, C.POINTER(LevelResult)]
+        L.mlmc_multilevel_sums_async.argtypes = [C.POINTER(LevelRequest), i32, i32,
+                                                 C.POINTER(Params), u64, vp, C.c_size_t, vp, vp]
+        L.mlmc_multilevel_sums.argtypes = [C.POINTER(LevelRequest), i32, i32, C.POINTER(Params),
+                                           u64, vp, C.c_size_t, vp, C.POINTER(LevelResult)]
+        L.mlmc_estimate.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t, vp,
+                                    C.POINTER(Result)]
+        L.mlmc_stmc_estimate.argtypes = [C.c_double, i32, i32, i32, C.POINTER(Params), u64, vp,
+                                         C.c_size_t, vp, C.POINTER(Result)]
+        L.mlmc_level_paths_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
+        L.mlmc_path_trace_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    try:
+        return lib().mlmc_strerror(code).decode()
+    except Exception:
+        return "status %d" % code
+
+
+def _check(rc, where, allow=()):
+    if rc != OK and rc not in allow:
+        raise MLMCError(rc, where)
+    return rc
+
+
+_PARAM_FIELDS = [f for f, _ in Params._fields_]
+
+
+def make_params(d=None, **kw):
+    """``Params`` from the library defaults, updated by a dict and keywords."""
+    p = Params()
+    lib().mlmc_params_default(C.byref(p))
+    for src in (d or {}), kw:
+        for k, v in src.items():
+            if k in _PARAM_FIELDS:
+                setattr(p, k, v)
+    return p
+
+
+def device_info():
+    out = (C.c_int32 * 3)()
+    _check(lib().mlmc_device_info(out), "mlmc_device_info")
+    return dict(sms=out[0], cc=out[1], version=out[2])
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Workspace:
+    """Device scratch owned by the caller (a torch uint8 tensor, 256-B aligned)."""
+
+    def __init__(self, params=None, max_requests=1, device=None):
+        import torch
+        p = params if params is not None else make_params()
+        self.nbytes = int(lib().mlmc_workspace_bytes(C.byref(p), max_requests))
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        self._buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self._buf.data_ptr()
+        self.ptr = (base + 255) // 256 * 256
+
+    def args(self):
+        return C.c_void_p(self.ptr), C.c_size_t(self.nbytes)
+
+
+def _level_result(r):
+    return dict(n=r.n, path_steps=r.path_steps, n_nonfinite=r.n_nonfinite,
+                sum=[[r.sum[q][j] for j in range(6)] for q in range(2)])
+
+
+def level_sums(level, N, integrator, params, seed, path_offset=0, workspace=None, stream=None):
+    """Sums of N coupled pairs of one level (``mlmc_level_sums``)."""
+    ws = workspace or Workspace(params)
+    r = LevelResult()
+    rc = lib().mlmc_level_sums(level, N, integrator, C.byref(params), seed, path_offset,
+                               *ws.args(), _stream_handle(stream), C.byref(r))
+    _check(rc, "mlmc_level_sums", allow=(ENONFINITE,))
+    return _level_result(r)
+
+
+def multilevel_sums(requests, integrator, params, seed, workspace=None, stream=None):
+    """Sums of many levels in one persistent launch; requests = [(level, first, count)]."""
+    n = len(requests)
+    ws = workspace or Workspace(params, n)
+    arr = (LevelRequest * n)()
+    for k, (lvl, first, count) in enumerate(requests):
+        arr[k].level, arr[k].first, arr[k].count = lvl, first, count
+    out = (LevelResult * n)()
+    rc = lib().mlmc_multilevel_sums(arr, n, integrator, C.byref(params), seed, *ws.args(),
+                                    _stream_handle(stream), out)
+    _check(rc, "mlmc_multilevel_sums", allow=(ENONFINITE,))
+    return [_level_result(out[k]) for k in range(n)]
+
+
+class MultilevelLaunch:
+    """Preplanned asynchronous batched launch with device-resident results.
+
+    ``run()`` enqueues the persistent kernel and the per-request reduction on
+    the stream and returns without synchronising; ``results()`` copies the
+    device results back.  Requests are sorted finest level first.
+    """
+
+    def __init__(self, requests, integrator, params, seed, workspace=None):
+        import torch
+        reqs = sorted(requests, key=lambda r: -r[0])
+        self.requests = reqs
+        self.n = len(reqs)
+        self.integrator = integrator
+        self.params = params
+        self.seed = seed
+        self.ws = workspace or Workspace(params, self.n)
+        self.arr = (LevelRequest * self.n)()
+        for k, (lvl, first, count) in enumerate(reqs):
+            self.arr[k].level, self.arr[k].first, self.arr[k].count = lvl, first, count
+        self.d_out = torch.zeros(self.n * C.sizeof(LevelResult), dtype=torch.uint8,
+                                 device=torch.device("cuda"))
+
+    def run(self, stream=None):
+        rc = lib().mlmc_multilevel_sums_async(self.arr, self.n, self.integrator,
+                                              C.byref(self.params), self.seed, *self.ws.args(),
+                                              _stream_handle(stream),
+                                              C.c_void_p(self.d_out.data_ptr()))
+        _check(rc, "mlmc_multilevel_sums_async")
+
+    def results(self):
+        raw = self.d_out.cpu().numpy().tobytes()
+        out = (LevelResult * self.n).from_buffer_copy(raw)
+        return [_level_result(out[k]) for k in range(self.n)]
+
+
+def _result(r, lmin):
+    L = r.L
+    return dict(estimate=list(r.estimate), est_variance=list(r.est_variance), L=L,
+                converged=r.converged, N=[r.N[l] for l in range(lmin, L + 1)],
+                V=[r.V[l] for l in range(lmin, L + 1)],
+                mean_y=[r.mean_y[l] for l in range(lmin, L + 1)],
+                total_path_steps=r.total_path_steps, n_nonfinite=r.n_nonfinite,
+                seconds=r.seconds)
+
+
+def estimate(eps, integrator, params, seed, workspace=None, stream=None):
+    """Adaptive MLMC estimate to RMSE eps (``mlmc_estimate``)."""
+    ws = workspace or Workspace(params)
+    r = Result()
+    rc = lib().mlmc_estimate(eps, integrator, C.byref(params), seed, *ws.args(),
+                             _stream_handle(stream), C.byref(r))
+    _check(rc, "mlmc_estimate", allow=(ENONFINITE, ENOTCONV))
+    out = _result(r, params.level_min)
+    out["status"] = rc
+    return out
+
+
+def stmc_estimate(eps, level, integrator, params, seed, n_pilot=10000, workspace=None,
+                  stream=None):
+    """Plain Monte Carlo at level's timestep to RMSE eps (``mlmc_stmc_estimate``)."""
+    ws = workspace or Workspace(params)
+    r = Result()
+    rc = lib().mlmc_stmc_estimate(eps, level, n_pilot, integrator, C.byref(params), seed,
+                                  *ws.args(), _stream_handle(stream), C.byref(r))
+    _check(rc, "mlmc_stmc_estimate", allow=(ENONFINITE,))
+    out = _result(r, level)
+    out["status"] = rc
+    return out
+
+
+def level_paths(level, N, integrator, params, seed, path_offset=0, stream=None):
+    """Final (z_f, w_f, z_c, w_c) of N pairs as an (N, 4) CUDA tensor, plus flags."""
+    import torch
+    dt = torch.float64 if params.precision == FP64 else torch.float32
+    states = torch.empty((N, 4), dtype=dt, device="cuda")
+    flags = torch.empty(N, dtype=torch.int32, device="cuda")
+    rc = lib().mlmc_level_paths_async(level, N, integrator, C.byref(params), seed, path_offset,
+                                      C.c_void_p(states.data_ptr()), C.c_void_p(flags.data_ptr()),
+                                      _stream_handle(stream))
+    _check(rc, "mlmc_level_paths_async")
+    return states, flags
+
+
+def path_trace(level, N, integrator, params, seed, path_offset=0, stream=None):
+    """Trajectories: (N, M+1, 3) fine and (N, M/2+1, 3) coarse CUDA tensors."""
+    import torch
+    dt = torch.float64 if params.precision == FP64 else torch.float32
+    M = params.M0 << level
+    tf = torch.zeros((N, M + 1, 3), dtype=dt, device="cuda")
+    tc = torch.zeros((N, M // 2 + 1, 3), dtype=dt, device="cuda")
+    rc = lib().mlmc_path_trace_async(level, N, integrator, C.byref(params), seed, path_offset,
+                                     C.c_void_p(tf.data_ptr()), C.c_void_p(tc.data_ptr()),
+                                     _stream_handle(stream))
+    _check(rc, "mlmc_path_trace_async")
+    return tf, tc

@@ -1,0 +1,714 @@
+// mlmc_api.cu -- the C ABI declared in include/mlmc.h: parameter checks,
+// workspace layout, the fixed-order reductions, and the host-driven MLMC and
+// plain Monte Carlo drivers.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "mlmc_internal.h"
+
+namespace mlmc {
+
+namespace prec_f32 {
+cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
+                       cudaStream_t);
+cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
+                       unsigned int*, int, cudaStream_t);
+cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*, int32_t*,
+                  void*, void*, bool, cudaStream_t);
+int occupancy(int, bool);
+}  // namespace prec_f32
+namespace prec_f64 {
+cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
+                       cudaStream_t);
+cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
+                       unsigned int*, int, cudaStream_t);
+cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*, int32_t*,
+                  void*, void*, bool, cudaStream_t);
+int occupancy(int, bool);
+}  // namespace prec_f64
+
+cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                              uint64_t N, uint64_t offset, Partial* partials, int grid,
+                              cudaStream_t st) {
+  return prec ? prec_f64::level_sums(integ, hm, lv, N, offset, partials, grid, st)
+              : prec_f32::level_sums(integ, hm, lv, N, offset, partials, grid, st);
+}
+cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
+                              int n_req, uint32_t n_items, Partial* partials,
+                              unsigned int* counter, int grid, cudaStream_t st) {
+  return prec ? prec_f64::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st)
+              : prec_f32::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
+}
+cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
+                         uint64_t offset, void* s, int32_t* f, cudaStream_t st) {
+  return prec ? prec_f64::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st)
+              : prec_f32::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st);
+}
+cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
+                         uint64_t offset, void* tf, void* tc, cudaStream_t st) {
+  return prec ? prec_f64::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st)
+              : prec_f32::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st);
+}
+int blocks_per_sm(int prec, int integ, bool multilevel) {
+  return prec ? prec_f64::occupancy(integ, multilevel) : prec_f32::occupancy(integ, multilevel);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-order reductions of block / item partials into mlmc_level_result.
+// One block per result; thread t takes partials t, t + 256, ... with Kahan
+// compensation, then the same warp tree and warp-ordered Kahan sum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kadd(double& s, double& c, double x) {
+  const double y = x - c;
+  const double t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint32_t end,
+                             uint64_t path_steps, mlmc_level_result* __restrict__ out) {
+  __shared__ double s_v[kBlock / 32][6];
+  __shared__ unsigned long long s_u[kBlock / 32][5];
+  double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long u[5] = {0, 0, 0, 0, 0};
+  for (uint32_t j = begin + threadIdx.x; j < end; j += kBlock) {
+    for (int k = 0; k < 6; ++k) kadd(s[k], c[k], p[j].s[k]);
+    u[0] += p[j].n; u[1] += p[j].bad; u[2] += p[j].nf; u[3] += p[j].nc; u[4] += p[j].nd;
+  }
+  double v[6];
+  for (int k = 0; k < 6; ++k) v[k] = s[k] - c[k];
+  for (int off = 16; off > 0; off >>= 1) {
+    for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+    for (int k = 0; k < 5; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    for (int k = 0; k < 6; ++k) s_v[warp][k] = v[k];
+    for (int k = 0; k < 5; ++k) s_u[warp][k] = u[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6] = {0, 0, 0, 0, 0, 0}, tc[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long q[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < kBlock / 32; ++w) {
+      for (int k = 0; k < 6; ++k) kadd(t[k], tc[k], s_v[w][k]);
+      for (int k = 0; k < 5; ++k) q[k] += s_u[w][k];
+    }
+    out->n = q[0];
+    out->n_nonfinite = q[1];
+    out->path_steps = path_steps;
+    out->reserved = 0;
+    for (int k = 0; k < 6; ++k) out->sum[0][k] = t[k] - tc[k];
+    const double nf = (double)q[2], nc = (double)q[3], nd = (double)q[4];
+    out->sum[1][0] = nf - nc;
+    out->sum[1][1] = nd;
+    out->sum[1][2] = nf;
+    out->sum[1][3] = nf;
+    out->sum[1][4] = nc;
+    out->sum[1][5] = nc;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_finalize(const Partial* __restrict__ p, uint32_t nb,
+                                                     uint64_t path_steps,
+                                                     mlmc_level_result* __restrict__ out) {
+  reduce_range(p, 0, nb, path_steps, out);
+}
+
+struct FinalizeMultiArgs {
+  uint32_t begin[kMaxReq], end[kMaxReq];
+  uint64_t path_steps[kMaxReq];
+};
+
+__global__ void __launch_bounds__(kBlock) k_finalize_multi(const Partial* __restrict__ p,
+                                                           const __grid_constant__ FinalizeMultiArgs a,
+                                                           mlmc_level_result* __restrict__ out) {
+  const int r = blockIdx.x;
+  reduce_range(p, a.begin[r], a.end[r], a.path_steps[r], out + r);
+}
+
+cudaError_t launch_finalize(const Partial* partials, int nblocks, uint64_t path_steps,
+                            mlmc_level_result* d_out, cudaStream_t st) {
+  k_finalize<<<1, kBlock, 0, st>>>(partials, (uint32_t)nblocks, path_steps, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, int n_req,
+                                  mlmc_level_result* d_out, cudaStream_t st) {
+  FinalizeMultiArgs a;
+  for (int r = 0; r < n_req; ++r) {
+    a.begin[r] = plan[r].item_base;
+    a.end[r] = plan[r].item_base + plan[r].n_items;
+    a.path_steps[r] = plan[r].path_steps;
+  }
+  k_finalize_multi<<<n_req, kBlock, 0, st>>>(partials, a, d_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Parameter checks and derived constants
+// ---------------------------------------------------------------------------
+static int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
+  if (!p) return MLMC_EINVAL;
+  const double us = p->u_star;
+  if (!(us > 0.0) || !(p->kappa_sigma > 0.0) || !(p->kappa_tau > 0.0)) return MLMC_EINVAL;
+  if (!(p->f_coriolis >= 0.0) || !(p->c_f >= 0.0)) return MLMC_EINVAL;
+  double H = p->H;
+  if (!(H > 0.0)) {
+    if (!(p->f_coriolis > 0.0)) return MLMC_EINVAL;
+    H = 0.3 * us / p->f_coriolis;
+  }
+  if (!std::isfinite(H)) return MLMC_EINVAL;
+  if (!(p->eps_reg_frac > 0.0) || !(p->eps_reg_frac <= 0.5)) return MLMC_EINVAL;
+  if (!(p->T > 0.0) || !std::isfinite(p->T)) return MLMC_EINVAL;
+  if (p->M0 < 1 || p->level_min < 0 || p->level_min > 40) return MLMC_EINVAL;
+  if (p->w0_mode < 0 || p->w0_mode > 2) return MLMC_EINVAL;
+  if (p->w0_mode != 2 && !(p->z0 >= 0.0 && p->z0 <= H)) return MLMC_EINVAL;
+  if (!std::isfinite(p->w0) || !std::isfinite(p->qoi_threshold)) return MLMC_EINVAL;
+  if (p->coupling < 0 || p->coupling > 1) return MLMC_EINVAL;
+  if (p->drift_outside < 0 || p->drift_outside > 1) return MLMC_EINVAL;
+  if (p->precision != MLMC_FP32 && p->precision != MLMC_FP64) return MLMC_EINVAL;
+  const double A = p->kappa_sigma * us;
+  hm->H = H;
+  hm->eps = p->eps_reg_frac * H;
+  hm->A = A;
+  hm->inv_ktau = 1.0 / p->kappa_tau;
+  hm->cfu = p->c_f * p->f_coriolis / us;
+  hm->hD = -0.75 * A * A / H;
+  hm->hDs = -0.75 / H;
+  hm->qthr = p->qoi_threshold;
+  hm->z0 = p->z0;
+  hm->w0 = p->w0;
+  hm->T = p->T;
+  hm->w0_mode = p->w0_mode;
+  hm->coupling = p->coupling;
+  hm->drift_outside = p->drift_outside;
+  hm->M0 = p->M0;
+  hm->level_min = p->level_min;
+  hm->stream_id = p->stream_id;
+  // Philox round keys: the key schedule adds the Weyl constants per round.
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    hm->rk0[r] = k0;
+    hm->rk1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return MLMC_OK;
+}
+
+static int level_spec(const HostModel& hm, int level, LevelSpec* ls) {
+  if (level < hm.level_min || level > 40) return MLMC_EINVAL;
+  const int64_t M = (int64_t)hm.M0 << level;
+  if (M <= 0 || M > ((int64_t)1 << 40)) return MLMC_EINVAL;
+  ls->level = level;
+  ls->M = M;
+  ls->h = hm.T / (double)M;
+  ls->coupled = level > hm.level_min;
+  if (ls->coupled && (M & 1)) return MLMC_EINVAL;
+  return MLMC_OK;
+}
+
+// lambda is largest at the regularisation height (it falls with z).
+static double lambda_max(const HostModel& hm) {
+  const double zc = hm.eps;
+  const double s = 1.0 - zc / hm.H;
+  const double sig = hm.A * std::pow(s, 0.75);
+  return sig * (1.0 + hm.cfu * zc) * hm.inv_ktau / zc;
+}
+
+static uint64_t steps_per_pair(const LevelSpec& ls) {
+  return ls.coupled ? (uint64_t)(ls.M + ls.M / 2) : (uint64_t)ls.M;
+}
+
+// ---------------------------------------------------------------------------
+// Device facts and workspace layout
+//   [0, 256)                  header: work counter
+//   [256, 256 + 32 * 128)     results of up to kMaxReq requests
+//   [..., + P * 128)          partials, P = max(blocks of one grid, kMaxItems)
+// ---------------------------------------------------------------------------
+struct DevInfo {
+  int sms = 0, cc = 0;
+};
+static DevInfo g_dev[64];
+static std::mutex g_mu;
+
+static int device_info(DevInfo* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MLMC_ENODEV;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_dev[dev].sms == 0) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return MLMC_ENODEV;
+    g_dev[dev].sms = prop.multiProcessorCount;
+    g_dev[dev].cc = prop.major * 10 + prop.minor;
+  }
+  *out = g_dev[dev];
+  return MLMC_OK;
+}
+
+static constexpr size_t kHeader = 256;
+static constexpr size_t kResults = (size_t)kMaxReq * sizeof(mlmc_level_result);
+static constexpr size_t kMaxGridBlocks = 4096;  // >= SMs * kMaxBlocksPerSM on GB300
+static size_t partial_slots() {
+  return kMaxGridBlocks > (size_t)kMaxItems ? kMaxGridBlocks : (size_t)kMaxItems;
+}
+static size_t workspace_needed() { return kHeader + kResults + partial_slots() * sizeof(Partial); }
+
+struct Workspace {
+  unsigned int* counter;
+  mlmc_level_result* results;
+  Partial* partials;
+};
+
+static int carve(void* ws, size_t bytes, Workspace* w) {
+  if (!ws || ((uintptr_t)ws & 255) != 0 || bytes < workspace_needed()) return MLMC_EWORKSPACE;
+  char* b = (char*)ws;
+  w->counter = (unsigned int*)b;
+  w->results = (mlmc_level_result*)(b + kHeader);
+  w->partials = (Partial*)(b + kHeader + kResults);
+  return MLMC_OK;
+}
+
+static int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
+  DevInfo di;
+  if (device_info(&di) != MLMC_OK) return 0;
+  int g = di.sms * blocks_per_sm(prec, integ, multilevel);
+  if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
+  if (!multilevel) {
+    const uint64_t need = (N + kBlock - 1) / kBlock;
+    if (need < (uint64_t)g) g = (int)(need > 0 ? need : 1);
+  }
+  return g;
+}
+
+static int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls) {
+  if (integ != MLMC_SE || p->allow_unstable) return MLMC_OK;
+  const double hmax = ls.coupled ? 2.0 * ls.h : ls.h;  // the coarse path steps 2h
+  return lambda_max(hm) * hmax < 2.0 ? MLMC_OK : MLMC_EUNSTABLE;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA; }
+
+// Eight independent FMA chains per thread; the operands come from memory so
+// nothing folds, and the results are stored so nothing is dropped.
+__global__ void __launch_bounds__(kBlock) k_ffma_probe(float* __restrict__ buf, int iters) {
+  const int t = blockIdx.x * kBlock + threadIdx.x;
+  const float b = buf[(t * 7) & 1023] * 1e-30f + 0.999f;
+  const float c = buf[(t * 13) & 1023] * 1e-30f + 1e-3f;
+  float a0 = t, a1 = t + 1, a2 = t + 2, a3 = t + 3, a4 = t + 4, a5 = t + 5, a6 = t + 6, a7 = t + 7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
+      a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+    }
+  }
+  buf[1024 + (t & ((1 << 20) - 1025))] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* mlmc_strerror(int code) {
+  switch (code) {
+    case MLMC_OK: return "success";
+    case MLMC_EINVAL: return "invalid argument or parameter";
+    case MLMC_EWORKSPACE: return "workspace missing, not 256-byte aligned, or too small";
+    case MLMC_ECUDA: return "CUDA call failed";
+    case MLMC_ENONFINITE: return "some paths diverged and were excluded";
+    case MLMC_ETIMEOUT: return "device work loop hit its iteration limit";
+    case MLMC_EUNSTABLE: return "symplectic Euler is unstable at this timestep (h lambda_max >= 2)";
+    case MLMC_ENOTCONV: return "adaptive driver reached L_max before its bias test passed";
+    case MLMC_ENODEV: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int mlmc_params_default(mlmc_params* p) {
+  if (!p) return MLMC_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->u_star = 0.2;
+  p->f_coriolis = 1e-4;
+  p->H = 600.0;
+  p->kappa_sigma = 1.3;
+  p->kappa_tau = 0.5;
+  p->c_f = 15.0;
+  p->eps_reg_frac = 1e-3;
+  p->z0 = 60.0;
+  p->w0 = 0.0;
+  p->T = 600.0;
+  p->qoi_threshold = 60.0;
+  p->w0_mode = 1;
+  p->M0 = 8;
+  p->level_min = 0;
+  p->L_max = 10;
+  p->coupling = 0;
+  p->drift_outside = 0;
+  p->n_init = 10000;
+  p->precision = MLMC_FP32;
+  p->stream_id = 0;
+  p->allow_unstable = 0;
+  return MLMC_OK;
+}
+
+int mlmc_device_info(int32_t out[3]) {
+  if (!out) return MLMC_EINVAL;
+  DevInfo di;
+  int rc = device_info(&di);
+  if (rc != MLMC_OK) return rc;
+  out[0] = di.sms;
+  out[1] = di.cc;
+  out[2] = 1;
+  return MLMC_OK;
+}
+
+size_t mlmc_workspace_bytes(const mlmc_params* p, int max_requests) {
+  (void)p;
+  (void)max_requests;
+  return workspace_needed();
+}
+
+int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p, uint64_t seed,
+                    uint64_t path_offset, void* workspace, size_t ws_bytes, void* stream,
+                    mlmc_level_result* out) {
+  if (!out || integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  Workspace w;
+  if ((rc = carve(workspace, ws_bytes, &w))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = p->precision;
+  const int grid = grid_for(prec, integrator, false, N);
+  if (grid <= 0) return MLMC_ENODEV;
+  if (N > (uint64_t)grid * kBlock * 0x7FFFFFFFull) return MLMC_EINVAL;  // per-thread counters
+  rc = cuda_status(launch_level_sums(prec, integrator, hm, ls, N, path_offset, w.partials, grid, st));
+  if (rc) return rc;
+  rc = cuda_status(launch_finalize(w.partials, grid, N * steps_per_pair(ls), w.results, st));
+  if (rc) return rc;
+  rc = cuda_status(cudaMemcpyAsync(out, w.results, sizeof(*out), cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  return out->n_nonfinite ? MLMC_ENONFINITE : MLMC_OK;
+}
+
+// Plan a multi-level launch: requests sorted by per-pair cost (finest level
+// first), split into items of about `target` path-steps.
+static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
+                         const mlmc_params* p, int grid, ReqPlan* plan, int* order,
+                         uint32_t* n_items_out) {
+  if (!reqs || n_req < 1 || n_req > kMaxReq) return MLMC_EINVAL;
+  double total = 0.0;
+  for (int r = 0; r < n_req; ++r) {
+    LevelSpec ls;
+    int rc = level_spec(hm, reqs[r].level, &ls);
+    if (rc) return rc;
+    if ((rc = check_stable(integ, p, hm, ls))) return rc;
+    total += (double)reqs[r].count * (double)steps_per_pair(ls);
+  }
+  for (int r = 0; r < n_req; ++r) order[r] = r;
+  // insertion sort by level, finest first (stable)
+  for (int i = 1; i < n_req; ++i) {
+    int v = order[i], j = i - 1;
+    while (j >= 0 && reqs[order[j]].level < reqs[v].level) { order[j + 1] = order[j]; --j; }
+    order[j + 1] = v;
+  }
+  // about 16 items per resident block, bounded by kMaxItems
+  double target = total / (16.0 * (double)grid);
+  if (target < 1.0) target = 1.0;
+  uint64_t items = 0;
+  for (int pass = 0; pass < 40; ++pass) {
+    items = 0;
+    for (int k = 0; k < n_req; ++k) {
+      const mlmc_level_request& q = reqs[order[k]];
+      LevelSpec ls;
+      level_spec(hm, q.level, &ls);
+      double ppi = std::floor(target / (double)steps_per_pair(ls));
+      uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+      if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
+      const uint64_t n_it = q.count ? (q.count + item_paths - 1) / item_paths : 0;
+      plan[k].lv = ls;
+      plan[k].first = q.first;
+      plan[k].count = q.count;
+      plan[k].item_paths = (uint32_t)item_paths;
+      plan[k].n_items = (uint32_t)n_it;
+      plan[k].item_base = (uint32_t)items;
+      plan[k].path_steps = q.count * steps_per_pair(ls);
+      items += n_it;
+    }
+    if (items <= (uint64_t)kMaxItems) break;
+    target *= 2.0;
+  }
+  if (items > (uint64_t)kMaxItems) return MLMC_EINVAL;
+  *n_items_out = (uint32_t)items;
+  return MLMC_OK;
+}
+
+static int multilevel_launch(const mlmc_level_request* reqs, int n_req, int integrator,
+                             const mlmc_params* p, uint64_t seed, void* workspace, size_t ws_bytes,
+                             cudaStream_t st, mlmc_level_result* d_sorted, ReqPlan* plan,
+                             int* order) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  Workspace w;
+  if ((rc = carve(workspace, ws_bytes, &w))) return rc;
+  const int prec = p->precision;
+  const int grid = grid_for(prec, integrator, true, 0);
+  if (grid <= 0) return MLMC_ENODEV;
+  uint32_t n_items = 0;
+  if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, plan, order, &n_items))) return rc;
+  rc = cuda_status(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), st));
+  if (rc) return rc;
+  rc = cuda_status(launch_multilevel(prec, integrator, hm, plan, n_req, n_items, w.partials,
+                                     w.counter, grid, st));
+  if (rc) return rc;
+  return cuda_status(launch_finalize_multi(w.partials, plan, n_req, d_sorted, st));
+}
+
+int mlmc_multilevel_sums_async(const mlmc_level_request* reqs, int n_req, int integrator,
+                               const mlmc_params* p, uint64_t seed, void* workspace,
+                               size_t ws_bytes, void* stream, mlmc_level_result* d_out) {
+  if (!d_out || !reqs || n_req < 1 || n_req > kMaxReq) return MLMC_EINVAL;
+  // requests must already be in non-increasing level order so that d_out
+  // lines up with reqs (the async form cannot permute on the device for free)
+  for (int r = 1; r < n_req; ++r)
+    if (reqs[r].level > reqs[r - 1].level) return MLMC_EINVAL;
+  ReqPlan plan[kMaxReq];
+  int order[kMaxReq];
+  return multilevel_launch(reqs, n_req, integrator, p, seed, workspace, ws_bytes,
+                           (cudaStream_t)stream, d_out, plan, order);
+}
+
+int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrator,
+                         const mlmc_params* p, uint64_t seed, void* workspace, size_t ws_bytes,
+                         void* stream, mlmc_level_result* out) {
+  if (!out || !reqs || n_req < 1 || n_req > kMaxReq) return MLMC_EINVAL;
+  ReqPlan plan[kMaxReq];
+  int order[kMaxReq];
+  Workspace w;
+  int rc = carve(workspace, ws_bytes, &w);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = multilevel_launch(reqs, n_req, integrator, p, seed, workspace, ws_bytes, st, w.results,
+                         plan, order);
+  if (rc) return rc;
+  mlmc_level_result tmp[kMaxReq];
+  rc = cuda_status(cudaMemcpyAsync(tmp, w.results, sizeof(mlmc_level_result) * n_req,
+                                   cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  uint64_t bad = 0;
+  for (int k = 0; k < n_req; ++k) {
+    out[order[k]] = tmp[k];
+    bad += tmp[k].n_nonfinite;
+  }
+  return bad ? MLMC_ENONFINITE : MLMC_OK;
+}
+
+// Adaptive MLMC (Giles 2008, Section 5; the rule the paper cites for N_l):
+//   1. L = level_min;  2. n_init samples on level L;  3. N_l = ceil(2 eps^-2
+//   sqrt(V_l / C_l) sum_k sqrt(V_k C_k));  4. run the extra samples;
+//   5. if L >= level_min + 2 stop when max(|Yhat_{L-1}| / 2, |Yhat_L|) <
+//   eps / sqrt(2);  6. else L += 1 (up to L_max) and go to 2.
+int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed, void* workspace,
+                  size_t ws_bytes, void* stream, mlmc_result* out) {
+  if (!out || !p || !(eps > 0.0)) return MLMC_EINVAL;
+  if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2)
+    return MLMC_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  mlmc_level_result S[MLMC_MAX_LEVELS];
+  uint64_t Ndone[MLMC_MAX_LEVELS] = {0}, dN[MLMC_MAX_LEVELS] = {0};
+  double V[MLMC_MAX_LEVELS] = {0}, C[MLMC_MAX_LEVELS] = {0};
+  std::memset(S, 0, sizeof(S));
+  const int lmin = p->level_min;
+  int L = lmin, converged = 0, status = MLMC_OK;
+  for (;;) {
+    dN[L] = (uint64_t)p->n_init;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int l = lmin; l <= L; ++l) {
+        if (!dN[l]) continue;
+        mlmc_level_result r;
+        int rc = mlmc_level_sums(l, dN[l], integrator, p, seed, Ndone[l], workspace, ws_bytes,
+                                 stream, &r);
+        if (rc == MLMC_ENONFINITE) status = MLMC_ENONFINITE;
+        else if (rc) return rc;
+        S[l].n += r.n;
+        S[l].n_nonfinite += r.n_nonfinite;
+        S[l].path_steps += r.path_steps;
+        for (int q = 0; q < 2; ++q)
+          for (int k = 0; k < 6; ++k) S[l].sum[q][k] += r.sum[q][k];
+        Ndone[l] += dN[l];
+        dN[l] = 0;
+      }
+      if (pass == 1) break;
+      double total = 0.0;
+      for (int l = lmin; l <= L; ++l) {
+        const double n = (double)S[l].n;
+        const double m1 = S[l].sum[0][0], m2 = S[l].sum[0][1];
+        V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
+        if (V[l] < 0.0) V[l] = 0.0;
+        const int64_t M = (int64_t)p->M0 << l;
+        C[l] = l > lmin ? (double)(M + M / 2) : (double)M;
+        total += std::sqrt(V[l] * C[l]);
+      }
+      for (int l = lmin; l <= L; ++l) {
+        const double Nopt = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * total);
+        dN[l] = Nopt > (double)Ndone[l] ? (uint64_t)(Nopt - (double)Ndone[l]) : 0;
+      }
+    }
+    if (L >= lmin + 2) {
+      const double yL = std::fabs(S[L].sum[0][0] / (double)S[L].n);
+      const double yL1 = std::fabs(S[L - 1].sum[0][0] / (double)S[L - 1].n);
+      if (std::fmax(yL1 / 2.0, yL) < eps / std::sqrt(2.0)) { converged = 1; break; }
+    }
+    if (L >= p->L_max) break;
+    L += 1;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->L = L;
+  out->converged = converged;
+  for (int q = 0; q < 2; ++q) {
+    double est = 0.0, var = 0.0;
+    for (int l = lmin; l <= L; ++l) {
+      const double n = (double)S[l].n;
+      const double m1 = S[l].sum[q][0], m2 = S[l].sum[q][1];
+      est += m1 / n;
+      const double v = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
+      var += (v > 0.0 ? v : 0.0) / n;
+    }
+    out->estimate[q] = est;
+    out->est_variance[q] = var;
+  }
+  for (int l = lmin; l <= L; ++l) {
+    const double n = (double)S[l].n;
+    out->N[l] = S[l].n;
+    out->mean_y[l] = S[l].sum[0][0] / n;
+    const double v = n > 1.0 ? (S[l].sum[0][1] - S[l].sum[0][0] * S[l].sum[0][0] / n) / (n - 1.0) : 0.0;
+    out->V[l] = v > 0.0 ? v : 0.0;
+    out->total_path_steps += S[l].path_steps;
+    out->n_nonfinite += S[l].n_nonfinite;
+  }
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (status) return status;
+  return converged ? MLMC_OK : MLMC_ENOTCONV;
+}
+
+// Plain Monte Carlo (Eq. StMCestimator) at one timestep: a pilot run sets
+// N = ceil(2 Var[P] / eps^2) (variance part of Eq. StMCerror at eps^2 / 2).
+int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator, const mlmc_params* p,
+                       uint64_t seed, void* workspace, size_t ws_bytes, void* stream,
+                       mlmc_result* out) {
+  if (!out || !p || !(eps > 0.0) || n_pilot < 2) return MLMC_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  mlmc_params q = *p;
+  q.level_min = level;  // plain paths on this level
+  mlmc_level_result a, b;
+  int status = MLMC_OK;
+  int rc = mlmc_level_sums(level, (uint64_t)n_pilot, integrator, &q, seed, 0, workspace, ws_bytes,
+                           stream, &a);
+  if (rc == MLMC_ENONFINITE) status = rc;
+  else if (rc) return rc;
+  const double n = (double)a.n;
+  double var = n > 1.0 ? (a.sum[0][1] - a.sum[0][0] * a.sum[0][0] / n) / (n - 1.0) : 0.0;
+  if (var < 0.0) var = 0.0;
+  const double Nt = std::ceil(2.0 * var / (eps * eps));
+  uint64_t extra = Nt > (double)n_pilot ? (uint64_t)(Nt - (double)n_pilot) : 0;
+  std::memset(&b, 0, sizeof(b));
+  if (extra) {
+    rc = mlmc_level_sums(level, extra, integrator, &q, seed, (uint64_t)n_pilot, workspace, ws_bytes,
+                         stream, &b);
+    if (rc == MLMC_ENONFINITE) status = rc;
+    else if (rc) return rc;
+  }
+  std::memset(out, 0, sizeof(*out));
+  const double nt = (double)(a.n + b.n);
+  for (int qq = 0; qq < 2; ++qq) {
+    const double m1 = a.sum[qq][0] + b.sum[qq][0], m2 = a.sum[qq][1] + b.sum[qq][1];
+    out->estimate[qq] = m1 / nt;
+    const double v = nt > 1.0 ? (m2 - m1 * m1 / nt) / (nt - 1.0) : 0.0;
+    out->est_variance[qq] = (v > 0.0 ? v : 0.0) / nt;
+  }
+  out->L = level;
+  out->converged = 1;
+  out->N[level] = a.n + b.n;
+  out->V[level] = var;
+  out->mean_y[level] = out->estimate[0];
+  out->total_path_steps = a.path_steps + b.path_steps;
+  out->n_nonfinite = a.n_nonfinite + b.n_nonfinite;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                           uint64_t seed, uint64_t path_offset, void* d_states, int32_t* d_flags,
+                           void* stream) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (N && (!d_states || !d_flags)) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  return cuda_status(launch_paths(p->precision, integrator, hm, ls, N, path_offset, d_states,
+                                  d_flags, (cudaStream_t)stream));
+}
+
+int mlmc_fp32_peak_probe(int iters, void* d_scratch, void* stream, double* flops_per_s) {
+  if (iters < 1 || !d_scratch || !flops_per_s) return MLMC_EINVAL;
+  DevInfo di;
+  int rc = device_info(&di);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = di.sms * kMaxBlocksPerSM;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MLMC_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MLMC_ECUDA; }
+  k_ffma_probe<<<grid, kBlock, 0, st>>>((float*)d_scratch, iters);  // warm-up
+  cudaEventRecord(e0, st);
+  k_ffma_probe<<<grid, kBlock, 0, st>>>((float*)d_scratch, iters);
+  cudaEventRecord(e1, st);
+  rc = cuda_status(cudaGetLastError());
+  if (!rc) rc = cuda_status(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  if (!rc) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  const double flops = 2.0 * 8.0 * 16.0 * (double)iters * (double)grid * kBlock;
+  *flops_per_s = flops / (ms * 1e-3);
+  return MLMC_OK;
+}
+
+int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                          uint64_t seed, uint64_t path_offset, void* d_trace_f, void* d_trace_c,
+                          void* stream) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (N && !d_trace_f) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  return cuda_status(launch_trace(p->precision, integrator, hm, ls, N, path_offset, d_trace_f,
+                                  d_trace_c, (cudaStream_t)stream));
+}
+
+}  // extern "C"

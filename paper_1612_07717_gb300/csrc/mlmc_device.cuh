@@ -1,0 +1,422 @@
+// mlmc_device.cuh -- device-side model of the MLMC boundary-layer dispersion
+// path for sm_103a: Philox4x32-10 normals, regularised profiles, the three
+// integrators with elastic reflection, and the coupled fine/coarse pair.
+//
+// One path pair lives in registers of one thread; nothing here touches
+// global memory except the optional trace writer.  R is float (the fast
+// path) or double (the FP64 baseline).
+//
+// References are to Katsiolides et al., arXiv 1612.07717.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mlmc {
+
+constexpr int kSE = 0, kGL = 1, kBAOAB = 2;
+
+// ---------------------------------------------------------------------------
+// Scenario constants, precomputed on the host for one parameter set.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Model {
+  R H, twoH, eps, Hme;  // depth, 2H, eps_reg, H - eps_reg
+  R invH;               // 1 / H
+  R A;                  // kappa_sigma u*                 (sigma_w = A s^{3/4})
+  R inv_ktau;           // 1 / kappa_tau
+  R cfu;                // c_f f / u*                      (Coriolis factor on tau)
+  R hD;                 // -3/4 A^2 / H : 1/2 d sigma_w^2/dz = hD s^{1/2}
+  R hDs;                // -3/4 / H     : 1/2 (d sigma_w^2/dz) / sigma_w^2 = hDs / s
+  R qthr;               // indicator threshold
+  R z0, w0;             // release state
+  R lim;                // 1e3 H: a path beyond it has diverged
+  int32_t w0_mode, coupling, drift_outside;
+  uint32_t stream_id;
+  uint32_t rk0[10], rk1[10];  // Philox round keys of the seed
+};
+
+// Per-level constants.
+template <typename R>
+struct Level {
+  R h, h2;            // fine step h and h / 2
+  R hc, hc2;          // coarse step 2h and h
+  int64_t M;          // fine steps
+  uint32_t c2;        // level word xored into counter word 2: level << 24
+  int32_t coupled;    // 0 on the coarsest level
+};
+
+// ---------------------------------------------------------------------------
+// Precision-generic primitives.  The float versions use the SFU (MUFU)
+// approximations; the double versions the IEEE routines.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float expneg_(float x) { return __expf(-x); }
+__device__ __forceinline__ double expneg_(double x) { return exp(-x); }
+__device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+
+// 1 - exp(-y) for y >= 0 without cancellation at small y.  Float: Taylor
+// series through y^7 below 1/4 (truncation < 4e-10 relative), 1 - exp(-y)
+// above (cancellation < 3e-7 relative).  Double: expm1.
+__device__ __forceinline__ float one_minus_expneg(float y) {
+  float s = 1.0f / 5040.0f;
+  s = fmaf(s, -y, 1.0f / 720.0f);
+  s = fmaf(s, -y, 1.0f / 120.0f);
+  s = fmaf(s, -y, 1.0f / 24.0f);
+  s = fmaf(s, -y, 1.0f / 6.0f);
+  s = fmaf(s, -y, 0.5f);
+  s = fmaf(s, -y, 1.0f);
+  float series = s * y;
+  float direct = 1.0f - __expf(-y);
+  return y < 0.25f ? series : direct;
+}
+__device__ __forceinline__ double one_minus_expneg(double y) { return -expm1(-y); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys of the
+// seed are precomputed on the host (they are the same for every thread).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(const uint32_t* __restrict__ rk0,
+                                         const uint32_t* __restrict__ rk1, uint32_t c0,
+                                         uint32_t c1, uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ rk0[r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rk1[r];
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Uniform maps.  Float: u = (floor(x / 2^9) + 1/2) 2^-23, formed exactly by
+// placing the top 23 bits in the mantissa of [1, 2) and subtracting
+// 1 - 2^-24 (Sterbenz: exact).  Double: u = (x + 1/2) 2^-32, exact.
+__device__ __forceinline__ float u01f(uint32_t x) {
+  return __uint_as_float((x >> 9) | 0x3F800000u) - 0.99999994039535522461f;
+}
+__device__ __forceinline__ double u01d(uint32_t x) {
+  return ((double)x + 0.5) * 2.3283064365386962890625e-10;
+}
+
+// Box-Muller on a word pair: R = sqrt(-2 ln u_a), angle 2 pi u_b.  The
+// float path evaluates the angle as 2 pi (u_b - 1/2) in (-pi, pi), where the
+// SFU sine and cosine are accurate, and negates (cos(t + pi) = -cos t).
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& na, float& nb) {
+  const float ua = u01f(xa), ub = u01f(xb);
+  const float s2 = -2.0f * __logf(ua);
+  const float r = s2 * rsqrtf(s2);
+  float sn, cs;
+  __sincosf(6.28318530717958647692f * (ub - 0.5f), &sn, &cs);
+  na = -r * cs;
+  nb = -r * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& na, double& nb) {
+  const double ua = u01d(xa), ub = u01d(xb);
+  const double r = sqrt(-2.0 * log(ua));
+  double sn, cs;
+  sincospi(2.0 * ub, &sn, &cs);
+  na = r * cs;
+  nb = r * sn;
+}
+__device__ __forceinline__ float uni_(uint32_t x, float) { return u01f(x); }
+__device__ __forceinline__ double uni_(uint32_t x, double) { return u01d(x); }
+
+// ---------------------------------------------------------------------------
+// Profiles, Eq. (profiles) with the cut-off of Eq. (regularisation).  With
+// s = 1 - z_c / H (z_c the clamped height), t = s^{-1/2}:
+//   sigma_w = A s^{3/4} = A (s t) rsqrt(t)
+//   lambda  = sigma_w (1 + c_f f z_c / u*) / (kappa_tau z_c)
+//   1/2 d sigma_w^2/dz          = -3/4 A^2 s^{1/2} / H = hD (s t)
+//   1/2 (d sigma_w^2/dz) / sigma_w^2 = -3/4 / (H s)   = hDs t^2
+// so the drift term -dV/dX = 1/2 (1 + w^2 / sigma_w^2) d sigma_w^2/dz is
+// g0 + g1 w^2 with g0 = hD s^{1/2}, g1 = hDs / s inside the band and 0
+// outside (the derivative of the frozen profile).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void profile(const Model<R>& m, R z, R& sig_u, R& lam, R& g0, R& g1) {
+  const R zc = fmin_(fmax_(z, m.eps), m.Hme);
+  const R s = fma(-zc, m.invH, R(1));
+  const R t = rsqrt_(s);
+  const R q = s * t;
+  const R r4 = rsqrt_(t);
+  sig_u = m.A * q * r4;
+  lam = sig_u * fma(m.cfu, zc, R(1)) * m.inv_ktau * rcp_(zc);
+  const bool use = ((z >= m.eps) && (z <= m.Hme)) || m.drift_outside;
+  g0 = use ? m.hD * q : R(0);
+  g1 = use ? m.hDs * (t * t) : R(0);
+}
+
+// Only the drift coefficients (the B half-steps of BAOAB).
+template <typename R>
+__device__ __forceinline__ void drift_coef(const Model<R>& m, R z, R& g0, R& g1) {
+  const R zc = fmin_(fmax_(z, m.eps), m.Hme);
+  const R s = fma(-zc, m.invH, R(1));
+  const R t = rsqrt_(s);
+  const bool use = ((z >= m.eps) && (z <= m.Hme)) || m.drift_outside;
+  g0 = use ? m.hD * (s * t) : R(0);
+  g1 = use ? m.hDs * (t * t) : R(0);
+}
+
+// ---------------------------------------------------------------------------
+// Elastic reflection (Section 4): z -> -z at the ground, z -> 2H - z at the
+// top, w -> -w, and the parity S = (-1)^{n_refl} flips.  One reflection is
+// done branch-free; the rare multi-reflection case loops (bounded).  A path
+// with |z| > 1e3 H (or NaN) is marked diverged, as in the oracle.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void reflect(const Model<R>& m, R& z, R& w, R& S, bool& bad) {
+  bad |= !(fabs(z) <= m.lim);
+  const bool lo = z < R(0), hi = z > m.H;
+  const R f = (lo || hi) ? R(-1) : R(1);
+  z = lo ? -z : (hi ? m.twoH - z : z);
+  w *= f;
+  S *= f;
+  if (z < R(0) || z > m.H) {
+    for (int it = 0; it < 2100 && (z < R(0) || z > m.H); ++it) {
+      if (!(fabs(z) <= m.lim)) { bad = true; break; }
+      z = (z < R(0)) ? -z : m.twoH - z;
+      w = -w;
+      S = -S;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One path: position, velocity, parity and (BAOAB) the cached drift terms
+// at the current position.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Path {
+  R z, w, S;
+  R g0, g1;
+};
+
+// Symplectic Euler, Eq. (MethodSymplecticEuler):
+//   w' = (1 - lambda h) w - dV/dX h + sigma sqrt(h) xi,  z' = z + w' h.
+template <typename R>
+__device__ __forceinline__ void se_step(const Model<R>& m, R h, Path<R>& p, bool& bad, R xi) {
+  R su, lam, g0, g1;
+  profile(m, p.z, su, lam, g0, g1);
+  const R amp = su * sqrt_(R(2) * lam * h);  // sigma sqrt(h), sigma^2 = 2 sigma_w^2 lambda
+  const R acc = fma(g1 * p.w, p.w, g0) - lam * p.w;
+  p.w = fma(amp, xi, fma(h, acc, p.w));
+  p.z = fma(p.w, h, p.z);
+  reflect(m, p.z, p.w, p.S, bad);
+}
+
+// O-step factors: e = exp(-lambda h) and the noise amplitude
+// sigma sqrt((1 - e^{-2 lambda h}) / (2 lambda)) = sigma_w sqrt(1 - e^2).
+template <typename R>
+__device__ __forceinline__ void ou_factors(R su, R lam, R h, R& e, R& c) {
+  const R x = lam * h;
+  e = expneg_(x);
+  c = su * sqrt_(one_minus_expneg(R(2) * x));
+}
+
+// Geometric Langevin (OBA), Eq. (MethodSymplecticEulerOU).  Returns e.
+template <typename R>
+__device__ __forceinline__ R gl_step(const Model<R>& m, R h, Path<R>& p, bool& bad, R xi) {
+  R su, lam, g0, g1, e, c;
+  profile(m, p.z, su, lam, g0, g1);
+  ou_factors(su, lam, h, e, c);
+  const R us = fma(c, xi, e * p.w);          // O
+  p.w = fma(h, fma(g1 * us, us, g0), us);    // B at (z_n, u*)
+  p.z = fma(p.w, h, p.z);                    // A
+  reflect(m, p.z, p.w, p.S, bad);
+  return e;
+}
+
+// BAOAB, Eq. (MethodBAOAB), folded after each A half-step.  The step is split
+// at the noise: baoab_pre runs B and A and leaves the parity of the O time in
+// p.S; baoab_post runs O, A, B.  p.g0 / p.g1 hold the drift terms at p.z.
+template <typename R>
+__device__ __forceinline__ void baoab_pre(const Model<R>& m, R h2, Path<R>& p, bool& bad) {
+  p.w = fma(h2, fma(p.g1 * p.w, p.w, p.g0), p.w);  // B half-step at z_n
+  p.z = fma(p.w, h2, p.z);                          // A half-step
+  reflect(m, p.z, p.w, p.S, bad);
+}
+template <typename R>
+__device__ __forceinline__ R baoab_post(const Model<R>& m, R h, R h2, Path<R>& p, bool& bad, R xi) {
+  R su, lam, g0, g1, e, c;
+  profile(m, p.z, su, lam, g0, g1);                 // at z_{n+1/2}
+  ou_factors(su, lam, h, e, c);
+  p.w = fma(c, xi, e * p.w);                        // O
+  p.z = fma(p.w, h2, p.z);                          // A half-step
+  reflect(m, p.z, p.w, p.S, bad);
+  drift_coef(m, p.z, p.g0, p.g1);                   // at z_{n+1}
+  p.w = fma(h2, fma(p.g1 * p.w, p.w, p.g0), p.w);   // B half-step
+  return e;
+}
+
+// Fine sub-step with normal xi; returns the parity at the noise time (Sn)
+// and the O-step factor e (GL/BAOAB) used by the coarse coupling.
+template <int INTEG, typename R>
+__device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
+                                          bool& bad, R xi, R& Sn, R& e) {
+  if (INTEG == kSE) {
+    Sn = p.S;
+    e = R(0);
+    se_step(m, lv.h, p, bad, xi);
+  } else if (INTEG == kGL) {
+    Sn = p.S;
+    e = gl_step(m, lv.h, p, bad, xi);
+  } else {
+    baoab_pre(m, lv.h2, p, bad);
+    Sn = p.S;
+    e = baoab_post(m, lv.h, lv.h2, p, bad, xi);
+  }
+}
+
+// Coarse step of 2h driven by the fine normals xa, xb of sub-steps 2k and
+// 2k+1 (parities Sa, Sb, O-factor ea of sub-step 2k):
+//   SE:       xi_c = S_c (S_a xa + S_b xb) / sqrt(2)          Eq. (euler_coupled_treatment)
+//   GL/BAOAB: xi_c = S_c (ea S_a xa + S_b xb) / sqrt(ea^2 + 1) Eq. (splitting_coupled_treatment)
+// With coupling = 1 (naive) all parities are taken as 1.
+template <int INTEG, typename R>
+__device__ __forceinline__ void coarse_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
+                                            bool& bad, R xa, R xb, R Sa, R Sb, R ea) {
+  if (m.coupling) { Sa = R(1); Sb = R(1); }
+  if (INTEG == kSE) {
+    const R Sc = m.coupling ? R(1) : p.S;
+    const R xc = (Sc * R(0.70710678118654752440)) * fma(Sa, xa, Sb * xb);
+    se_step(m, lv.hc, p, bad, xc);
+  } else if (INTEG == kGL) {
+    const R Sc = m.coupling ? R(1) : p.S;
+    const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
+    gl_step(m, lv.hc, p, bad, xc);
+  } else {
+    baoab_pre(m, lv.hc2, p, bad);
+    const R Sc = m.coupling ? R(1) : p.S;
+    const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
+    baoab_post(m, lv.hc, lv.hc2, p, bad, xc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (shared by the fine and coarse path): fixed, w0 ~
+// N(0, sigma_w(z0)^2), or the well-mixed state; the draws come from the
+// reserved counter block 0xFFFFFFFF.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void initial_state(const Model<R>& m, const Level<R>& lv, uint32_t i_lo,
+                                              uint32_t i_hi, R& z, R& w) {
+  z = m.z0;
+  w = m.w0;
+  if (m.w0_mode == 0) return;
+  const uint4 x = philox10(m.rk0, m.rk1, 0xFFFFFFFFu, i_lo, i_hi ^ lv.c2, m.stream_id);
+  R na, nb;
+  box_muller(x.x, x.y, na, nb);
+  if (m.w0_mode == 2) z = m.H * uni_(x.z, R(0));
+  R su, lam, g0, g1;
+  profile(m, z, su, lam, g0, g1);
+  w = su * na;
+}
+
+// Trace sink: the production kernels pass NoTrace.
+template <typename R>
+struct NoTrace {
+  __device__ __forceinline__ void fine(int64_t, const Path<R>&) const {}
+  __device__ __forceinline__ void coarse(int64_t, const Path<R>&) const {}
+};
+template <typename R>
+struct Trace {
+  R* f;  // (M+1) x 3
+  R* c;  // (M/2+1) x 3 or null
+  __device__ __forceinline__ void fine(int64_t row, const Path<R>& p) const {
+    f[3 * row] = p.z; f[3 * row + 1] = p.w; f[3 * row + 2] = p.S;
+  }
+  __device__ __forceinline__ void coarse(int64_t row, const Path<R>& p) const {
+    if (c) { c[3 * row] = p.z; c[3 * row + 1] = p.w; c[3 * row + 2] = p.S; }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// One path pair of a level (Section 3.2): fine path with M steps and, on
+// coupled levels, the coarse path with M/2 steps driven by the same Brownian
+// increments.  Normal n of the fine path is word n mod 4 of Philox block n/4.
+// ---------------------------------------------------------------------------
+template <int INTEG, typename R, bool COUPLED, class TR>
+__device__ __forceinline__ void run_pair(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                         Path<R>& f, Path<R>& c, bool& bad, const TR& tr) {
+  const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
+  const uint32_t w2 = i_hi ^ lv.c2;
+  R z0, w0;
+  initial_state(m, lv, i_lo, i_hi, z0, w0);
+  f.z = z0; f.w = w0; f.S = R(1);
+  f.g0 = R(0); f.g1 = R(0);
+  if (INTEG == kBAOAB) drift_coef(m, z0, f.g0, f.g1);
+  c = f;
+  bad = false;
+  tr.fine(0, f);
+  if (COUPLED) tr.coarse(0, c);
+  const int64_t M = lv.M;
+  const int64_t nblk = M >> 2;
+  R Sa, Sb, ea, eb;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const uint4 x = philox10(m.rk0, m.rk1, (uint32_t)b, i_lo, w2, m.stream_id);
+    R xi0, xi1, xi2, xi3;
+    box_muller(x.x, x.y, xi0, xi1);
+    box_muller(x.z, x.w, xi2, xi3);
+    if (COUPLED) {
+      fine_step<INTEG>(m, lv, f, bad, xi0, Sa, ea);
+      tr.fine(4 * b + 1, f);
+      fine_step<INTEG>(m, lv, f, bad, xi1, Sb, eb);
+      tr.fine(4 * b + 2, f);
+      coarse_step<INTEG>(m, lv, c, bad, xi0, xi1, Sa, Sb, ea);
+      tr.coarse(2 * b + 1, c);
+      fine_step<INTEG>(m, lv, f, bad, xi2, Sa, ea);
+      tr.fine(4 * b + 3, f);
+      fine_step<INTEG>(m, lv, f, bad, xi3, Sb, eb);
+      tr.fine(4 * b + 4, f);
+      coarse_step<INTEG>(m, lv, c, bad, xi2, xi3, Sa, Sb, ea);
+      tr.coarse(2 * b + 2, c);
+    } else {
+      fine_step<INTEG>(m, lv, f, bad, xi0, Sa, ea);
+      tr.fine(4 * b + 1, f);
+      fine_step<INTEG>(m, lv, f, bad, xi1, Sa, ea);
+      tr.fine(4 * b + 2, f);
+      fine_step<INTEG>(m, lv, f, bad, xi2, Sa, ea);
+      tr.fine(4 * b + 3, f);
+      fine_step<INTEG>(m, lv, f, bad, xi3, Sa, ea);
+      tr.fine(4 * b + 4, f);
+    }
+  }
+  const int tail = (int)(M & 3);  // fine steps left when M is not a multiple of 4
+  if (tail) {
+    const uint4 x = philox10(m.rk0, m.rk1, (uint32_t)nblk, i_lo, w2, m.stream_id);
+    R xi[4];
+    box_muller(x.x, x.y, xi[0], xi[1]);
+    box_muller(x.z, x.w, xi[2], xi[3]);
+    const int64_t n0 = 4 * nblk;
+    if (COUPLED) {
+      // M even: tail is 2, one coarse step
+      fine_step<INTEG>(m, lv, f, bad, xi[0], Sa, ea);
+      tr.fine(n0 + 1, f);
+      fine_step<INTEG>(m, lv, f, bad, xi[1], Sb, eb);
+      tr.fine(n0 + 2, f);
+      coarse_step<INTEG>(m, lv, c, bad, xi[0], xi[1], Sa, Sb, ea);
+      tr.coarse(n0 / 2 + 1, c);
+    } else {
+      for (int j = 0; j < tail; ++j) {
+        fine_step<INTEG>(m, lv, f, bad, xi[j], Sa, ea);
+        tr.fine(n0 + j + 1, f);
+      }
+    }
+  }
+  bad |= !(isfinite(f.z) && isfinite(f.w));
+  if (COUPLED) bad |= !(isfinite(c.z) && isfinite(c.w));
+}
+
+}  // namespace mlmc

@@ -1,0 +1,69 @@
+// mlmc_internal.h -- host-side interface between the C ABI (mlmc_api.cu) and
+// the kernel translation units (one per path precision).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mlmc.h"
+
+namespace mlmc {
+
+constexpr int kBlock = 256;          // threads per block of every path kernel
+constexpr int kMaxReq = 32;          // requests in one multi-level launch
+constexpr int kMaxItems = 32768;     // work items in one multi-level launch
+constexpr int kMaxBlocksPerSM = 8;   // 2048 threads / kBlock
+
+// Partial sums of one thread block (or one work item), 128 bytes.
+struct Partial {
+  double s[6];  // QoI 0: sum Y, Y^2, P_f, P_f^2, P_c, P_c^2 (compensated)
+  unsigned long long n, bad, nf, nc, nd;  // QoI 1 counts: P_f = 1, P_c = 1, P_f != P_c
+  unsigned long long pad[5];
+};
+static_assert(sizeof(Partial) == 128, "Partial layout");
+static_assert(sizeof(mlmc_level_result) == 128, "mlmc_level_result layout");
+
+// Scenario in double precision, derived once from mlmc_params.
+struct HostModel {
+  double H, eps, A, inv_ktau, cfu, hD, hDs, qthr, z0, w0, T;
+  int32_t w0_mode, coupling, drift_outside, M0, level_min;
+  uint32_t stream_id;
+  uint32_t rk0[10], rk1[10];
+};
+
+struct LevelSpec {
+  int level;
+  int64_t M;
+  double h;
+  bool coupled;
+};
+
+// One request of a multi-level launch after planning on the host.
+struct ReqPlan {
+  LevelSpec lv;
+  uint64_t first, count;
+  uint32_t item_paths, n_items, item_base;
+  uint64_t path_steps;
+};
+
+// Kernel launchers, implemented per precision (prec: 0 float, 1 double).
+cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                              uint64_t N, uint64_t offset, Partial* partials, int grid,
+                              cudaStream_t st);
+cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
+                              int n_req, uint32_t n_items, Partial* partials,
+                              unsigned int* counter, int grid, cudaStream_t st);
+cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                         uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
+                         cudaStream_t st);
+cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                         uint64_t N, uint64_t offset, void* d_tf, void* d_tc, cudaStream_t st);
+// Resident blocks per SM of the sums / multi-level kernels (occupancy query).
+int blocks_per_sm(int prec, int integ, bool multilevel);
+
+// Precision-independent reductions (mlmc_api.cu).
+cudaError_t launch_finalize(const Partial* partials, int nblocks, uint64_t path_steps,
+                            mlmc_level_result* d_out, cudaStream_t st);
+cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, int n_req,
+                                  mlmc_level_result* d_out, cudaStream_t st);
+
+}  // namespace mlmc

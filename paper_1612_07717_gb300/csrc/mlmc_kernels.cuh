@@ -1,0 +1,368 @@
+// mlmc_kernels.cuh -- the path kernels, instantiated once per precision by
+// mlmc_kernels_f32.cu and mlmc_kernels_f64.cu.
+//
+//   k_level_sums  coupled-level kernel: a grid-stride loop of path pairs,
+//                 per-thread FP64 accumulation (Kahan on sum Y and sum Y^2),
+//                 a block reduction into one Partial per block.
+//   k_multilevel  persistent multi-level kernel: blocks pull fixed-size work
+//                 items of any level from an atomic counter (items ordered
+//                 by per-path cost, finest level first) and write one
+//                 Partial per item, so the sums do not depend on scheduling.
+//   k_paths       final states per pair (validation and per-particle output)
+//   k_trace       full trajectories (validation)
+#pragma once
+#include "mlmc_device.cuh"
+#include "mlmc_internal.h"
+
+namespace mlmc {
+
+// ---------------------------------------------------------------------------
+// Host -> device constants
+// ---------------------------------------------------------------------------
+template <typename R>
+Model<R> make_model(const HostModel& h) {
+  Model<R> m;
+  m.H = (R)h.H;
+  m.twoH = (R)(2.0 * h.H);
+  m.eps = (R)h.eps;
+  m.Hme = (R)(h.H - h.eps);
+  m.invH = (R)(1.0 / h.H);
+  m.A = (R)h.A;
+  m.inv_ktau = (R)h.inv_ktau;
+  m.cfu = (R)h.cfu;
+  m.hD = (R)h.hD;
+  m.hDs = (R)h.hDs;
+  m.qthr = (R)h.qthr;
+  m.z0 = (R)h.z0;
+  m.w0 = (R)h.w0;
+  m.lim = (R)(1e3 * h.H);
+  m.w0_mode = h.w0_mode;
+  m.coupling = h.coupling;
+  m.drift_outside = h.drift_outside;
+  m.stream_id = h.stream_id;
+  for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
+  return m;
+}
+
+template <typename R>
+Level<R> make_level(const LevelSpec& s) {
+  Level<R> l;
+  l.h = (R)s.h;
+  l.h2 = (R)(0.5 * s.h);
+  l.hc = (R)(2.0 * s.h);
+  l.hc2 = (R)s.h;
+  l.M = s.M;
+  l.c2 = (uint32_t)s.level << 24;
+  l.coupled = s.coupled ? 1 : 0;
+  return l;
+}
+
+// ---------------------------------------------------------------------------
+// Per-thread accumulator and block reduction
+// ---------------------------------------------------------------------------
+struct Acc {
+  double y, cy, y2, cy2;   // Kahan pairs: sum Y, sum Y^2 of QoI 0
+  double pf, pf2, pc, pc2;
+  uint32_t n, bad, nf, nc, nd;
+};
+
+__device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
+  const double y = x - c;
+  const double t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ void acc_zero(Acc& a) {
+  a.y = a.cy = a.y2 = a.cy2 = a.pf = a.pf2 = a.pc = a.pc2 = 0.0;
+  a.n = a.bad = a.nf = a.nc = a.nd = 0;
+}
+
+// QoIs at T (Section 3.2): P = z(T) and P = 1[z(T) < threshold]; the
+// indicator decision is taken in the path precision.
+template <typename R, bool COUPLED>
+__device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, bool bad) {
+  if (bad) { a.bad += 1; return; }
+  const double Pf = (double)zf;
+  const double Pc = COUPLED ? (double)zc : 0.0;
+  const double Y = Pf - Pc;
+  kahan_add(a.y, a.cy, Y);
+  kahan_add(a.y2, a.cy2, Y * Y);
+  a.pf += Pf; a.pf2 += Pf * Pf;
+  a.pc += Pc; a.pc2 += Pc * Pc;
+  const bool If = zf < m.qthr;
+  const bool Ic = COUPLED && (zc < m.qthr);
+  a.nf += If; a.nc += Ic; a.nd += (If != Ic);
+  a.n += 1;
+}
+
+// Warp tree (fixed order), then warp 0's lane 0 adds the warp results in
+// warp order with Kahan compensation.  Ends with the block synchronised.
+__device__ __forceinline__ void block_reduce_store(const Acc& a, Partial* __restrict__ out) {
+  __shared__ double s_v[kBlock / 32][6];
+  __shared__ unsigned long long s_u[kBlock / 32][5];
+  double v[6] = {a.y - a.cy, a.y2 - a.cy2, a.pf, a.pf2, a.pc, a.pc2};
+  unsigned long long u[5] = {a.n, a.bad, a.nf, a.nc, a.nd};
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_v[warp][k] = v[k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s_u[warp][k] = u[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long t[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < kBlock / 32; ++w) {
+      for (int k = 0; k < 6; ++k) kahan_add(s[k], c[k], s_v[w][k]);
+      for (int k = 0; k < 5; ++k) t[k] += s_u[w][k];
+    }
+    for (int k = 0; k < 6; ++k) out->s[k] = s[k] - c[k];
+    out->n = t[0]; out->bad = t[1]; out->nf = t[2]; out->nc = t[3]; out->nd = t[4];
+    for (int k = 0; k < 5; ++k) out->pad[k] = 0;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Coupled-level sums
+// ---------------------------------------------------------------------------
+template <typename R>
+struct SumsArgs {
+  Model<R> m;
+  Level<R> lv;
+  uint64_t N, offset;
+  Partial* partials;
+};
+
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
+  Acc acc;
+  acc_zero(acc);
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < a.N; j += stride) {
+    Path<R> f, c;
+    bool bad;
+    run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
+    acc_add<R, COUPLED>(acc, a.m, f.z, c.z, bad);
+  }
+  block_reduce_store(acc, a.partials + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent multi-level kernel
+// ---------------------------------------------------------------------------
+template <typename R>
+struct ReqDev {
+  Level<R> lv;
+  uint64_t first, count;
+  uint32_t item_paths, n_items, item_base, pad;
+};
+
+template <typename R>
+struct MultiArgs {
+  Model<R> m;
+  ReqDev<R> req[kMaxReq];
+  int32_t n_req;
+  uint32_t n_items;
+  Partial* partials;
+  unsigned int* counter;
+};
+
+template <int INTEG, typename R, bool COUPLED>
+__device__ __forceinline__ void multilevel_item(const Model<R>& m, const ReqDev<R>& rq,
+                                                uint64_t first, uint32_t count, Acc& acc) {
+  for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
+    Path<R> f, c;
+    bool bad;
+    run_pair<INTEG, R, COUPLED>(m, rq.lv, first + j, f, c, bad, NoTrace<R>());
+    acc_add<R, COUPLED>(acc, m, f.z, c.z, bad);
+  }
+}
+
+template <int INTEG, typename R>
+__global__ void __launch_bounds__(kBlock) k_multilevel(const __grid_constant__ MultiArgs<R> a) {
+  __shared__ unsigned int s_item;
+  // Every block does at most n_items iterations: the loop ends when the
+  // shared counter passes the last item; there is no waiting on other blocks.
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned int it = s_item;
+    __syncthreads();
+    if (it >= a.n_items) break;
+    int r = 0;
+    while (r + 1 < a.n_req && it >= a.req[r + 1].item_base) ++r;
+    const ReqDev<R>& rq = a.req[r];
+    const uint32_t local = it - rq.item_base;
+    const uint64_t start = (uint64_t)local * rq.item_paths;
+    const uint64_t left = rq.count - start;
+    const uint32_t count = (uint32_t)(left < rq.item_paths ? left : rq.item_paths);
+    Acc acc;
+    acc_zero(acc);
+    if (rq.lv.coupled)
+      multilevel_item<INTEG, R, true>(a.m, rq, rq.first + start, count, acc);
+    else
+      multilevel_item<INTEG, R, false>(a.m, rq, rq.first + start, count, acc);
+    block_reduce_store(acc, a.partials + it);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-path outputs
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PathsArgs {
+  Model<R> m;
+  Level<R> lv;
+  uint64_t N, offset;
+  R* states;        // N x 4
+  int32_t* flags;   // N
+  R* tf;            // trace: N x (M+1) x 3
+  R* tc;            // trace: N x (M/2+1) x 3
+};
+
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock) k_paths(const __grid_constant__ PathsArgs<R> a) {
+  const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (j >= a.N) return;
+  Path<R> f, c;
+  bool bad;
+  run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
+  R* o = a.states + 4 * j;
+  o[0] = f.z; o[1] = f.w;
+  o[2] = COUPLED ? c.z : R(0);
+  o[3] = COUPLED ? c.w : R(0);
+  a.flags[j] = bad ? 1 : 0;
+}
+
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ PathsArgs<R> a) {
+  const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (j >= a.N) return;
+  const int64_t M = a.lv.M;
+  Trace<R> tr;
+  tr.f = a.tf + (uint64_t)3 * (M + 1) * j;
+  tr.c = (COUPLED && a.tc) ? a.tc + (uint64_t)3 * (M / 2 + 1) * j : nullptr;
+  Path<R> f, c;
+  bool bad;
+  run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, tr);
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch helpers
+// ---------------------------------------------------------------------------
+template <typename R, template <int, typename, bool> class K, typename Args>
+cudaError_t launch3(int integ, bool coupled, dim3 grid, const Args& args, cudaStream_t st) {
+#define MLMC_LAUNCH(I)                                                        \
+  if (coupled) K<I, R, true>::launch(grid, args, st);                          \
+  else K<I, R, false>::launch(grid, args, st);
+  if (integ == kSE) { MLMC_LAUNCH(kSE) }
+  else if (integ == kGL) { MLMC_LAUNCH(kGL) }
+  else { MLMC_LAUNCH(kBAOAB) }
+#undef MLMC_LAUNCH
+  return cudaGetLastError();
+}
+
+template <int I, typename R, bool C>
+struct SumsK {
+  static void launch(dim3 g, const SumsArgs<R>& a, cudaStream_t st) {
+    k_level_sums<I, R, C><<<g, kBlock, 0, st>>>(a);
+  }
+};
+template <int I, typename R, bool C>
+struct PathsK {
+  static void launch(dim3 g, const PathsArgs<R>& a, cudaStream_t st) {
+    k_paths<I, R, C><<<g, kBlock, 0, st>>>(a);
+  }
+};
+template <int I, typename R, bool C>
+struct TraceK {
+  static void launch(dim3 g, const PathsArgs<R>& a, cudaStream_t st) {
+    k_trace<I, R, C><<<g, kBlock, 0, st>>>(a);
+  }
+};
+
+template <typename R>
+cudaError_t level_sums_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
+                            uint64_t offset, Partial* partials, int grid, cudaStream_t st) {
+  SumsArgs<R> a;
+  a.m = make_model<R>(hm);
+  a.lv = make_level<R>(ls);
+  a.N = N;
+  a.offset = offset;
+  a.partials = partials;
+  return launch3<R, SumsK>(integ, ls.coupled, dim3(grid), a, st);
+}
+
+template <typename R>
+cudaError_t multilevel_impl(int integ, const HostModel& hm, const ReqPlan* plan, int n_req,
+                            uint32_t n_items, Partial* partials, unsigned int* counter, int grid,
+                            cudaStream_t st) {
+  MultiArgs<R> a;
+  a.m = make_model<R>(hm);
+  for (int r = 0; r < n_req; ++r) {
+    a.req[r].lv = make_level<R>(plan[r].lv);
+    a.req[r].first = plan[r].first;
+    a.req[r].count = plan[r].count;
+    a.req[r].item_paths = plan[r].item_paths;
+    a.req[r].n_items = plan[r].n_items;
+    a.req[r].item_base = plan[r].item_base;
+    a.req[r].pad = 0;
+  }
+  a.n_req = n_req;
+  a.n_items = n_items;
+  a.partials = partials;
+  a.counter = counter;
+  if (integ == kSE) k_multilevel<kSE, R><<<grid, kBlock, 0, st>>>(a);
+  else if (integ == kGL) k_multilevel<kGL, R><<<grid, kBlock, 0, st>>>(a);
+  else k_multilevel<kBAOAB, R><<<grid, kBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t paths_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
+                       uint64_t offset, void* states, int32_t* flags, void* tf, void* tc,
+                       bool trace, cudaStream_t st) {
+  PathsArgs<R> a;
+  a.m = make_model<R>(hm);
+  a.lv = make_level<R>(ls);
+  a.N = N;
+  a.offset = offset;
+  a.states = (R*)states;
+  a.flags = flags;
+  a.tf = (R*)tf;
+  a.tc = (R*)tc;
+  const dim3 g((unsigned)((N + kBlock - 1) / kBlock));
+  if (N == 0) return cudaSuccess;
+  if (trace) return launch3<R, TraceK>(integ, ls.coupled, g, a, st);
+  return launch3<R, PathsK>(integ, ls.coupled, g, a, st);
+}
+
+template <typename R>
+int blocks_per_sm_impl(int integ, bool multilevel) {
+  int nb = 0;
+  cudaError_t e;
+  if (multilevel) {
+    if (integ == kSE) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multilevel<kSE, R>, kBlock, 0);
+    else if (integ == kGL) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multilevel<kGL, R>, kBlock, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multilevel<kBAOAB, R>, kBlock, 0);
+  } else {
+    if (integ == kSE) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level_sums<kSE, R, true>, kBlock, 0);
+    else if (integ == kGL) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level_sums<kGL, R, true>, kBlock, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level_sums<kBAOAB, R, true>, kBlock, 0);
+  }
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  if (nb > kMaxBlocksPerSM) nb = kMaxBlocksPerSM;
+  return nb;
+}
+
+}  // namespace mlmc

@@ -1,0 +1,21 @@
+// mlmc_kernels_f64.cu -- double-precision instantiation of the path kernels.
+#include "mlmc_kernels.cuh"
+
+namespace mlmc {
+namespace prec_f64 {
+cudaError_t level_sums(int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
+                       uint64_t offset, Partial* partials, int grid, cudaStream_t st) {
+  return level_sums_impl<double>(integ, hm, lv, N, offset, partials, grid, st);
+}
+cudaError_t multilevel(int integ, const HostModel& hm, const ReqPlan* plan, int n_req,
+                       uint32_t n_items, Partial* partials, unsigned int* counter, int grid,
+                       cudaStream_t st) {
+  return multilevel_impl<double>(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
+}
+cudaError_t paths(int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N, uint64_t offset,
+                  void* states, int32_t* flags, void* tf, void* tc, bool trace, cudaStream_t st) {
+  return paths_impl<double>(integ, hm, lv, N, offset, states, flags, tf, tc, trace, st);
+}
+int occupancy(int integ, bool multilevel) { return blocks_per_sm_impl<double>(integ, multilevel); }
+}  // namespace prec_f64
+}  // namespace mlmc
