@@ -176,6 +176,34 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
                          const mlmc_params* p, uint64_t seed, void* workspace,
                          size_t ws_bytes, void* stream, mlmc_level_result* out);
 
+/* The batched launch of mlmc_multilevel_sums_async for callers that cannot
+ * allocate device memory at all: a framework that owns every byte of device
+ * memory through its own pool, a latency-bound loop that must never call
+ * cudaMalloc (it can synchronise the whole device), or an embedded host with
+ * a fixed memory budget.  The paper has no counterpart; this is an interface
+ * convenience.
+ *
+ * Instead of a caller workspace it uses one array of device memory that the
+ * library defines statically: 256 + 4096 * 128 bytes (about 0.5 MiB), held
+ * on every GPU that loads the library until the process exits.  The work is
+ * split into at most 4096 items (items are enlarged to fit); a batch that
+ * cannot be split that way (more than 4096 * (2^31 - 1) pairs) returns
+ * MLMC_EWORKSPACE, more than 32 requests MLMC_EINVAL.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The first call on each device looks up the array's device address once
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture begins.  All calls share the one array and it
+ * keeps the last call's contents: the call clears the work counter itself,
+ * but two calls that overlap on the GPU (different streams, no ordering
+ * between them) race on the array, so order them on one stream or with
+ * events.  Arguments, results and ordering rules otherwise as
+ * mlmc_multilevel_sums_async: reqs in non-increasing level order, d_out a
+ * device array of n_req results, no synchronisation. */
+int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req, int integrator,
+                                 const mlmc_params* p, uint64_t seed, void* stream,
+                                 mlmc_level_result* d_out);
+
 /* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Section 3.2 and the
  * sample-size rule of Giles 2008 the paper adopts in Section 5): levels are
  * added from level_min, N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k

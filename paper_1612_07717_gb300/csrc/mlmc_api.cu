@@ -712,3 +712,109 @@ int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_para
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batched launch without any allocation: the scratch lives in a fixed array
+// of device memory that belongs to this library.
+// ===========================================================================
+namespace mlmc {
+
+// Upper bound on the work items of one call; each item needs one 128-byte
+// partial slot, so the array is 256 + 4096 * 128 bytes (about 0.5 MiB).  Every
+// GPU that loads the library keeps this array until the process exits.
+constexpr int kNoAllocItems = 4096;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[256 + kNoAllocItems * sizeof(Partial)];
+
+// Device address of the array, looked up once per device with that device
+// current.  Host code cannot use the symbol itself: on the host it names a
+// stand-in, not device memory.
+static void* g_noalloc_ptr[64];
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MLMC_ENODEV;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MLMC_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MLMC_OK;
+}
+
+// Same split as the workspace form (finest level first, about 16 items per
+// resident block), enlarging the items until the plan fits kNoAllocItems.
+static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
+                        const mlmc_params* p, int grid, ReqPlan* plan, uint32_t* n_items_out) {
+  double total = 0.0;
+  for (int r = 0; r < n_req; ++r) {
+    LevelSpec ls;
+    int rc = level_spec(hm, reqs[r].level, &ls);
+    if (rc) return rc;
+    if ((rc = check_stable(integ, p, hm, ls))) return rc;
+    total += (double)reqs[r].count * (double)steps_per_pair(ls);
+  }
+  double target = total / (16.0 * (double)grid);
+  if (target < 1.0) target = 1.0;
+  for (int pass = 0; pass < 64; ++pass) {
+    uint64_t items = 0;
+    bool too_big = false;
+    for (int k = 0; k < n_req; ++k) {
+      LevelSpec ls;
+      level_spec(hm, reqs[k].level, &ls);
+      const double ppi = std::floor(target / (double)steps_per_pair(ls));
+      uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+      if (item_paths > 0x7FFFFFFFull) { item_paths = 0x7FFFFFFFull; too_big = true; }
+      const uint64_t n_it = reqs[k].count ? (reqs[k].count + item_paths - 1) / item_paths : 0;
+      plan[k].lv = ls;
+      plan[k].first = reqs[k].first;
+      plan[k].count = reqs[k].count;
+      plan[k].item_paths = (uint32_t)item_paths;
+      plan[k].n_items = (uint32_t)n_it;
+      plan[k].item_base = (uint32_t)items;
+      plan[k].path_steps = reqs[k].count * steps_per_pair(ls);
+      items += n_it;
+    }
+    if (items <= (uint64_t)kNoAllocItems) {
+      *n_items_out = (uint32_t)items;
+      return MLMC_OK;
+    }
+    if (too_big) break;
+    target *= 2.0;
+  }
+  return MLMC_EWORKSPACE;  // more than kNoAllocItems items of 2^31 - 1 pairs
+}
+
+}  // namespace mlmc
+
+extern "C" int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req,
+                                            int integrator, const mlmc_params* p, uint64_t seed,
+                                            void* stream, mlmc_level_result* d_out) {
+  if (!d_out || !reqs || n_req < 1 || n_req > kMaxReq) return MLMC_EINVAL;
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  for (int r = 1; r < n_req; ++r)
+    if (reqs[r].level > reqs[r - 1].level) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  const int prec = p->precision;
+  const int grid = grid_for(prec, integrator, true, 0);
+  if (grid <= 0) return MLMC_ENODEV;
+  ReqPlan plan[kMaxReq];
+  uint32_t n_items = 0;
+  if ((rc = plan_noalloc(hm, reqs, n_req, integrator, p, grid, plan, &n_items))) return rc;
+  unsigned int* counter = (unsigned int*)scratch;
+  Partial* partials = (Partial*)((char*)scratch + 256);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the work counter must start at zero; every partial slot the reduction
+  // reads is written first by its item, so nothing else needs clearing
+  rc = cuda_status(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st));
+  if (rc) return rc;
+  rc = cuda_status(launch_multilevel(prec, integrator, hm, plan, n_req, n_items, partials, counter,
+                                     grid, st));
+  if (rc) return rc;
+  return cuda_status(launch_finalize_multi(partials, plan, n_req, d_out, st));
+}
