@@ -212,6 +212,33 @@ int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req, int 
 int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed,
                   void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
 
+/* The same adaptive estimate with the whole loop on the device, as one CUDA
+ * graph: an init kernel, then a conditional while-node whose body is the
+ * persistent multi-level kernel over the levels that need samples, the
+ * fixed-order per-level reduction, and a one-thread update kernel that adds
+ * the sums, applies N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)),
+ * the bias test and the next plan, and sets the loop condition.  The driver
+ * state, plan and result live in the workspace (which must stay alive and
+ * unused by other calls while the graph runs).  The loop is bounded: at most
+ * 4 * MLMC_MAX_LEVELS passes, else MLMC_ETIMEOUT.
+ *   mlmc_graph_create   builds and instantiates the graph (host work; no
+ *                       kernel runs yet); returns an opaque handle
+ *   mlmc_graph_launch   enqueues one complete estimate on `stream`
+ *   mlmc_graph_result   copies the result of the last launch into *out and
+ *                       synchronises `stream`; same codes as mlmc_estimate
+ *   mlmc_graph_destroy  frees the handle (host resources only)
+ * mlmc_estimate_graph does all four once.  The graph's estimate equals
+ * mlmc_estimate's up to the FP64 rounding of the level sums (the batched
+ * kernel groups paths into items differently). */
+typedef struct mlmc_graph_s* mlmc_graph;
+int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                      void* workspace, size_t ws_bytes, mlmc_graph* out);
+int mlmc_graph_launch(mlmc_graph g, void* stream);
+int mlmc_graph_result(mlmc_graph g, void* stream, mlmc_result* out);
+int mlmc_graph_destroy(mlmc_graph g);
+int mlmc_estimate_graph(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                        void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
+
 /* Plain Monte Carlo (Eq. StMCestimator) at `level`'s timestep to RMSE eps:
  * n_pilot paths estimate Var[P], then N = ceil(2 Var / eps^2) in total. */
 int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator,

@@ -94,6 +94,13 @@ def lib():
                                            u64, vp, C.c_size_t, vp, C.POINTER(LevelResult)]
         L.mlmc_estimate.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t, vp,
                                     C.POINTER(Result)]
+        L.mlmc_graph_create.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
+                                        C.POINTER(vp)]
+        L.mlmc_graph_launch.argtypes = [vp, vp]
+        L.mlmc_graph_result.argtypes = [vp, vp, C.POINTER(Result)]
+        L.mlmc_graph_destroy.argtypes = [vp]
+        L.mlmc_estimate_graph.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
+                                          vp, C.POINTER(Result)]
         L.mlmc_stmc_estimate.argtypes = [C.c_double, i32, i32, i32, C.POINTER(Params), u64, vp,
                                          C.c_size_t, vp, C.POINTER(Result)]
         L.mlmc_level_paths_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
@@ -243,6 +250,52 @@ def estimate(eps, integrator, params, seed, workspace=None, stream=None):
     out = _result(r, params.level_min)
     out["status"] = rc
     return out
+
+
+def estimate_graph(eps, integrator, params, seed, workspace=None, stream=None):
+    """Adaptive MLMC estimate with the loop captured in one CUDA graph."""
+    ws = workspace or Workspace(params)
+    r = Result()
+    rc = lib().mlmc_estimate_graph(eps, integrator, C.byref(params), seed, *ws.args(),
+                                   _stream_handle(stream), C.byref(r))
+    _check(rc, "mlmc_estimate_graph", allow=(ENONFINITE, ENOTCONV))
+    out = _result(r, params.level_min)
+    out["status"] = rc
+    return out
+
+
+class GraphEstimator:
+    """An instantiated graph of the adaptive loop, launched many times."""
+
+    def __init__(self, eps, integrator, params, seed, workspace=None):
+        self.params = params
+        self.ws = workspace or Workspace(params)
+        self.handle = C.c_void_p()
+        rc = lib().mlmc_graph_create(eps, integrator, C.byref(params), seed, *self.ws.args(),
+                                     C.byref(self.handle))
+        _check(rc, "mlmc_graph_create")
+
+    def launch(self, stream=None):
+        _check(lib().mlmc_graph_launch(self.handle, _stream_handle(stream)), "mlmc_graph_launch")
+
+    def result(self, stream=None):
+        r = Result()
+        rc = lib().mlmc_graph_result(self.handle, _stream_handle(stream), C.byref(r))
+        _check(rc, "mlmc_graph_result", allow=(ENONFINITE, ENOTCONV))
+        out = _result(r, self.params.level_min)
+        out["status"] = rc
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().mlmc_graph_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stmc_estimate(eps, level, integrator, params, seed, n_pilot=10000, workspace=None,

@@ -11,6 +11,8 @@
 namespace mlmc {
 
 namespace prec_f32 {
+cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
+                           cudaStream_t);
 cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
                        cudaStream_t);
 cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
@@ -20,6 +22,8 @@ cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, v
 int occupancy(int, bool);
 }  // namespace prec_f32
 namespace prec_f64 {
+cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
+                           cudaStream_t);
 cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
                        cudaStream_t);
 cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
@@ -40,6 +44,12 @@ cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const Re
                               unsigned int* counter, int grid, cudaStream_t st) {
   return prec ? prec_f64::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st)
               : prec_f32::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
+}
+cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, const DevPlan* plan,
+                                  Partial* partials, unsigned int* counter, int grid,
+                                  cudaStream_t st) {
+  return prec ? prec_f64::multilevel_dev(integ, hm, plan, partials, counter, grid, st)
+              : prec_f32::multilevel_dev(integ, hm, plan, partials, counter, grid, st);
 }
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                          uint64_t offset, void* s, int32_t* f, cudaStream_t st) {
@@ -129,6 +139,22 @@ __global__ void __launch_bounds__(kBlock) k_finalize_multi(const Partial* __rest
   reduce_range(p, a.begin[r], a.end[r], a.path_steps[r], out + r);
 }
 
+// Reduction of a device-planned launch: one block per planned request.
+__global__ void __launch_bounds__(kBlock) k_finalize_dev(const Partial* __restrict__ p,
+                                                         const DevPlan* __restrict__ plan,
+                                                         mlmc_level_result* __restrict__ out) {
+  const int r = blockIdx.x;
+  if (r >= plan->n_req) return;
+  const PlanReq& q = plan->req[r];
+  reduce_range(p, q.item_base, q.item_base + q.n_items, q.path_steps, out + r);
+}
+
+cudaError_t launch_finalize_dev(const Partial* partials, const DevPlan* plan,
+                                mlmc_level_result* d_out, cudaStream_t st) {
+  k_finalize_dev<<<kMaxReq, kBlock, 0, st>>>(partials, plan, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const Partial* partials, int nblocks, uint64_t path_steps,
                             mlmc_level_result* d_out, cudaStream_t st) {
   k_finalize<<<1, kBlock, 0, st>>>(partials, (uint32_t)nblocks, path_steps, d_out);
@@ -150,7 +176,7 @@ cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, 
 // ---------------------------------------------------------------------------
 // Parameter checks and derived constants
 // ---------------------------------------------------------------------------
-static int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
+int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
   if (!p) return MLMC_EINVAL;
   const double us = p->u_star;
   if (!(us > 0.0) || !(p->kappa_sigma > 0.0) || !(p->kappa_tau > 0.0)) return MLMC_EINVAL;
@@ -199,7 +225,7 @@ static int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
   return MLMC_OK;
 }
 
-static int level_spec(const HostModel& hm, int level, LevelSpec* ls) {
+int level_spec(const HostModel& hm, int level, LevelSpec* ls) {
   if (level < hm.level_min || level > 40) return MLMC_EINVAL;
   const int64_t M = (int64_t)hm.M0 << level;
   if (M <= 0 || M > ((int64_t)1 << 40)) return MLMC_EINVAL;
@@ -219,7 +245,7 @@ static double lambda_max(const HostModel& hm) {
   return sig * (1.0 + hm.cfu * zc) * hm.inv_ktau / zc;
 }
 
-static uint64_t steps_per_pair(const LevelSpec& ls) {
+uint64_t steps_per_pair(const LevelSpec& ls) {
   return ls.coupled ? (uint64_t)(ls.M + ls.M / 2) : (uint64_t)ls.M;
 }
 
@@ -229,13 +255,10 @@ static uint64_t steps_per_pair(const LevelSpec& ls) {
 //   [256, 256 + 32 * 128)     results of up to kMaxReq requests
 //   [..., + P * 128)          partials, P = max(blocks of one grid, kMaxItems)
 // ---------------------------------------------------------------------------
-struct DevInfo {
-  int sms = 0, cc = 0;
-};
 static DevInfo g_dev[64];
 static std::mutex g_mu;
 
-static int device_info(DevInfo* out) {
+int device_info(DevInfo* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MLMC_ENODEV;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -255,24 +278,21 @@ static constexpr size_t kMaxGridBlocks = 4096;  // >= SMs * kMaxBlocksPerSM on G
 static size_t partial_slots() {
   return kMaxGridBlocks > (size_t)kMaxItems ? kMaxGridBlocks : (size_t)kMaxItems;
 }
-static size_t workspace_needed() { return kHeader + kResults + partial_slots() * sizeof(Partial); }
+size_t workspace_needed() {
+  return kHeader + kResults + partial_slots() * sizeof(Partial) + kGraphRegion;
+}
 
-struct Workspace {
-  unsigned int* counter;
-  mlmc_level_result* results;
-  Partial* partials;
-};
-
-static int carve(void* ws, size_t bytes, Workspace* w) {
+int carve(void* ws, size_t bytes, Workspace* w) {
   if (!ws || ((uintptr_t)ws & 255) != 0 || bytes < workspace_needed()) return MLMC_EWORKSPACE;
   char* b = (char*)ws;
   w->counter = (unsigned int*)b;
   w->results = (mlmc_level_result*)(b + kHeader);
   w->partials = (Partial*)(b + kHeader + kResults);
+  w->graph = b + kHeader + kResults + partial_slots() * sizeof(Partial);
   return MLMC_OK;
 }
 
-static int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
+int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
   DevInfo di;
   if (device_info(&di) != MLMC_OK) return 0;
   int g = di.sms * blocks_per_sm(prec, integ, multilevel);
@@ -284,13 +304,13 @@ static int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
   return g;
 }
 
-static int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls) {
+int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls) {
   if (integ != MLMC_SE || p->allow_unstable) return MLMC_OK;
   const double hmax = ls.coupled ? 2.0 * ls.h : ls.h;  // the coarse path steps 2h
   return lambda_max(hm) * hmax < 2.0 ? MLMC_OK : MLMC_EUNSTABLE;
 }
 
-static int cuda_status(cudaError_t e) { return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA; }
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA; }
 
 // Eight independent FMA chains per thread; the operands come from memory so
 // nothing folds, and the results are stored so nothing is dropped.

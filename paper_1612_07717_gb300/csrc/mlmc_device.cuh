@@ -4,7 +4,10 @@
 //
 // One path pair lives in registers of one thread; nothing here touches
 // global memory except the optional trace writer.  R is float (the fast
-// path) or double (the FP64 baseline).
+// path) or double (the FP64 baseline).  The kernels are issue-bound, so the
+// step code is written to keep the instruction count low: the reflection is
+// branch-free, the O-step factors share one exponential, and the profile
+// needs three SFU operations.
 //
 // References are to Katsiolides et al., arXiv 1612.07717.
 #pragma once
@@ -23,14 +26,14 @@ struct Model {
   R H, twoH, eps, Hme;  // depth, 2H, eps_reg, H - eps_reg
   R invH;               // 1 / H
   R A;                  // kappa_sigma u*                 (sigma_w = A s^{3/4})
-  R inv_ktau;           // 1 / kappa_tau
-  R cfu;                // c_f f / u*                      (Coriolis factor on tau)
-  R hD;                 // -3/4 A^2 / H : 1/2 d sigma_w^2/dz = hD s^{1/2}
-  R hDs;                // -3/4 / H     : 1/2 (d sigma_w^2/dz) / sigma_w^2 = hDs / s
+  R Akt;                // A / kappa_tau                  (lambda = Akt s^{3/4} (1/z + c_f f/u*))
+  R cfu;                // c_f f / u*
+  R hD, hD_out;         // 1/2 d sigma_w^2/dz = hD s^{1/2} inside the band (hD_out outside)
+  R hDs, hDs_out;       // 1/2 (d sigma_w^2/dz) / sigma_w^2 = hDs / s inside (hDs_out outside)
   R qthr;               // indicator threshold
   R z0, w0;             // release state
   R lim;                // 1e3 H: a path beyond it has diverged
-  int32_t w0_mode, coupling, drift_outside;
+  int32_t w0_mode, coupling;
   uint32_t stream_id;
   uint32_t rk0[10], rk1[10];  // Philox round keys of the seed
 };
@@ -62,22 +65,21 @@ __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
 
-// 1 - exp(-y) for y >= 0 without cancellation at small y.  Float: Taylor
-// series through y^7 below 1/4 (truncation < 4e-10 relative), 1 - exp(-y)
-// above (cancellation < 3e-7 relative).  Double: expm1.
-__device__ __forceinline__ float one_minus_expneg(float y) {
-  float s = 1.0f / 5040.0f;
-  s = fmaf(s, -y, 1.0f / 720.0f);
-  s = fmaf(s, -y, 1.0f / 120.0f);
-  s = fmaf(s, -y, 1.0f / 24.0f);
-  s = fmaf(s, -y, 1.0f / 6.0f);
-  s = fmaf(s, -y, 0.5f);
-  s = fmaf(s, -y, 1.0f);
-  float series = s * y;
-  float direct = 1.0f - __expf(-y);
-  return y < 0.25f ? series : direct;
+// 1 - exp(-2x) for x >= 0 given e = exp(-x), without cancellation at small
+// x.  Float: Taylor series of 1 - e^{-2x} through x^5 below x = 0.05
+// (truncation < 1.5e-8 relative), 1 - e*e above (cancellation < 7e-7
+// relative).  Double: expm1.
+__device__ __forceinline__ float one_minus_e2(float x, float e) {
+  float s = 4.0f / 15.0f;
+  s = fmaf(s, x, -2.0f / 3.0f);
+  s = fmaf(s, x, 4.0f / 3.0f);
+  s = fmaf(s, x, -2.0f);
+  s = fmaf(s, x, 2.0f);
+  const float series = s * x;
+  const float direct = fmaf(-e, e, 1.0f);
+  return x < 0.05f ? series : direct;
 }
-__device__ __forceinline__ double one_minus_expneg(double y) { return -expm1(-y); }
+__device__ __forceinline__ double one_minus_e2(double x, double) { return -expm1(-2.0 * x); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys of the
@@ -135,62 +137,81 @@ __device__ __forceinline__ double uni_(uint32_t x, double) { return u01d(x); }
 
 // ---------------------------------------------------------------------------
 // Profiles, Eq. (profiles) with the cut-off of Eq. (regularisation).  With
-// s = 1 - z_c / H (z_c the clamped height), t = s^{-1/2}:
+// z_c the clamped height, s = 1 - z_c / H and t = s^{-1/2}:
 //   sigma_w = A s^{3/4} = A (s t) rsqrt(t)
 //   lambda  = sigma_w (1 + c_f f z_c / u*) / (kappa_tau z_c)
-//   1/2 d sigma_w^2/dz          = -3/4 A^2 s^{1/2} / H = hD (s t)
-//   1/2 (d sigma_w^2/dz) / sigma_w^2 = -3/4 / (H s)   = hDs t^2
+//           = (A / kappa_tau) s^{3/4} (1 / z_c + c_f f / u*)
+//   1/2 d sigma_w^2/dz               = -3/4 A^2 s^{1/2} / H = hD (s t)
+//   1/2 (d sigma_w^2/dz) / sigma_w^2 = -3/4 / (H s)        = hDs t^2
 // so the drift term -dV/dX = 1/2 (1 + w^2 / sigma_w^2) d sigma_w^2/dz is
-// g0 + g1 w^2 with g0 = hD s^{1/2}, g1 = hDs / s inside the band and 0
-// outside (the derivative of the frozen profile).
+// g0 + g1 w^2.  Outside the band (z_c != z) the derivative of the frozen
+// profile is 0 (hD_out = hDs_out = 0) unless the frozen-value reading is
+// selected.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void profile(const Model<R>& m, R z, R& sig_u, R& lam, R& g0, R& g1) {
   const R zc = fmin_(fmax_(z, m.eps), m.Hme);
+  const bool inb = zc == z;
   const R s = fma(-zc, m.invH, R(1));
   const R t = rsqrt_(s);
   const R q = s * t;
-  const R r4 = rsqrt_(t);
-  sig_u = m.A * q * r4;
-  lam = sig_u * fma(m.cfu, zc, R(1)) * m.inv_ktau * rcp_(zc);
-  const bool use = ((z >= m.eps) && (z <= m.Hme)) || m.drift_outside;
-  g0 = use ? m.hD * q : R(0);
-  g1 = use ? m.hDs * (t * t) : R(0);
+  const R s34 = q * rsqrt_(t);
+  sig_u = m.A * s34;
+  lam = (m.Akt * s34) * (rcp_(zc) + m.cfu);
+  g0 = (inb ? m.hD : m.hD_out) * q;
+  g1 = (inb ? m.hDs : m.hDs_out) * (t * t);
 }
 
 // Only the drift coefficients (the B half-steps of BAOAB).
 template <typename R>
 __device__ __forceinline__ void drift_coef(const Model<R>& m, R z, R& g0, R& g1) {
   const R zc = fmin_(fmax_(z, m.eps), m.Hme);
+  const bool inb = zc == z;
   const R s = fma(-zc, m.invH, R(1));
   const R t = rsqrt_(s);
-  const bool use = ((z >= m.eps) && (z <= m.Hme)) || m.drift_outside;
-  g0 = use ? m.hD * (s * t) : R(0);
-  g1 = use ? m.hDs * (t * t) : R(0);
+  g0 = (inb ? m.hD : m.hD_out) * (s * t);
+  g1 = (inb ? m.hDs : m.hDs_out) * (t * t);
 }
 
 // ---------------------------------------------------------------------------
 // Elastic reflection (Section 4): z -> -z at the ground, z -> 2H - z at the
-// top, w -> -w, and the parity S = (-1)^{n_refl} flips.  One reflection is
-// done branch-free; the rare multi-reflection case loops (bounded).  A path
-// with |z| > 1e3 H (or NaN) is marked diverged, as in the oracle.
+// top, w -> -w, and the parity S = (-1)^{n_refl} flips.
+//
+// reflect_fast: one reflection, branch-free and exact: z' = min(|z|, 2H - |z|)
+// equals z inside [0, H], -z below, 2H - z above; a reflection happened iff
+// z' != z.  It equals the oracle's fold for z in [-H, 2H]; outside that range
+// (more than one reflection) it sets the sticky `multi` flag, and the caller
+// replays the whole path with reflect_exact.  (Steps that cross more than one layer depth only occur on
+// paths that are diverging.)
+//
+// reflect_exact: the loop of single reflections, as in the oracle, with
+// |z| > 1e3 H (or NaN) marking the path as diverged.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void reflect(const Model<R>& m, R& z, R& w, R& S, bool& bad) {
-  bad |= !(fabs(z) <= m.lim);
-  const bool lo = z < R(0), hi = z > m.H;
-  const R f = (lo || hi) ? R(-1) : R(1);
-  z = lo ? -z : (hi ? m.twoH - z : z);
-  w *= f;
-  S *= f;
-  if (z < R(0) || z > m.H) {
-    for (int it = 0; it < 2100 && (z < R(0) || z > m.H); ++it) {
-      if (!(fabs(z) <= m.lim)) { bad = true; break; }
-      z = (z < R(0)) ? -z : m.twoH - z;
-      w = -w;
-      S = -S;
-    }
+__device__ __forceinline__ void reflect_fast(const Model<R>& m, R& z, R& w, R& S, bool& multi) {
+  const R za = fabs(z);
+  const R zr = fmin_(za, m.twoH - za);
+  const bool flip = zr != z;
+  w = flip ? -w : w;
+  S = flip ? -S : S;
+  multi |= (z < -m.H) | (zr < R(0));  // exact tests of z outside [-H, 2H]
+  z = zr;
+}
+
+template <typename R>
+__device__ __forceinline__ void reflect_exact(const Model<R>& m, R& z, R& w, R& S, bool& bad) {
+  for (int it = 0; it < 2100 && (z < R(0) || z > m.H); ++it) {
+    if (!(fabs(z) <= m.lim)) { bad = true; return; }
+    z = (z < R(0)) ? -z : m.twoH - z;
+    w = -w;
+    S = -S;
   }
+}
+
+template <typename R, bool EXACT>
+__device__ __forceinline__ void reflect(const Model<R>& m, R& z, R& w, R& S, bool& flag) {
+  if (EXACT) reflect_exact(m, z, w, S, flag);
+  else reflect_fast(m, z, w, S, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,16 +225,17 @@ struct Path {
 };
 
 // Symplectic Euler, Eq. (MethodSymplecticEuler):
-//   w' = (1 - lambda h) w - dV/dX h + sigma sqrt(h) xi,  z' = z + w' h.
-template <typename R>
-__device__ __forceinline__ void se_step(const Model<R>& m, R h, Path<R>& p, bool& bad, R xi) {
+//   w' = (1 - lambda h) w - dV/dX h + sigma sqrt(h) xi,  z' = z + w' h,
+// with sigma sqrt(h) = sigma_w sqrt(2 lambda h).
+template <typename R, bool EX>
+__device__ __forceinline__ void se_step(const Model<R>& m, R h, Path<R>& p, bool& flag, R xi) {
   R su, lam, g0, g1;
   profile(m, p.z, su, lam, g0, g1);
-  const R amp = su * sqrt_(R(2) * lam * h);  // sigma sqrt(h), sigma^2 = 2 sigma_w^2 lambda
-  const R acc = fma(g1 * p.w, p.w, g0) - lam * p.w;
+  const R amp = su * sqrt_((R(2) * h) * lam);
+  const R acc = fma(-lam, p.w, fma(g1 * p.w, p.w, g0));
   p.w = fma(amp, xi, fma(h, acc, p.w));
   p.z = fma(p.w, h, p.z);
-  reflect(m, p.z, p.w, p.S, bad);
+  reflect<R, EX>(m, p.z, p.w, p.S, flag);
 }
 
 // O-step factors: e = exp(-lambda h) and the noise amplitude
@@ -222,39 +244,39 @@ template <typename R>
 __device__ __forceinline__ void ou_factors(R su, R lam, R h, R& e, R& c) {
   const R x = lam * h;
   e = expneg_(x);
-  c = su * sqrt_(one_minus_expneg(R(2) * x));
+  c = su * sqrt_(one_minus_e2(x, e));
 }
 
 // Geometric Langevin (OBA), Eq. (MethodSymplecticEulerOU).  Returns e.
-template <typename R>
-__device__ __forceinline__ R gl_step(const Model<R>& m, R h, Path<R>& p, bool& bad, R xi) {
+template <typename R, bool EX>
+__device__ __forceinline__ R gl_step(const Model<R>& m, R h, Path<R>& p, bool& flag, R xi) {
   R su, lam, g0, g1, e, c;
   profile(m, p.z, su, lam, g0, g1);
   ou_factors(su, lam, h, e, c);
   const R us = fma(c, xi, e * p.w);          // O
   p.w = fma(h, fma(g1 * us, us, g0), us);    // B at (z_n, u*)
   p.z = fma(p.w, h, p.z);                    // A
-  reflect(m, p.z, p.w, p.S, bad);
+  reflect<R, EX>(m, p.z, p.w, p.S, flag);
   return e;
 }
 
 // BAOAB, Eq. (MethodBAOAB), folded after each A half-step.  The step is split
 // at the noise: baoab_pre runs B and A and leaves the parity of the O time in
 // p.S; baoab_post runs O, A, B.  p.g0 / p.g1 hold the drift terms at p.z.
-template <typename R>
-__device__ __forceinline__ void baoab_pre(const Model<R>& m, R h2, Path<R>& p, bool& bad) {
+template <typename R, bool EX>
+__device__ __forceinline__ void baoab_pre(const Model<R>& m, R h2, Path<R>& p, bool& flag) {
   p.w = fma(h2, fma(p.g1 * p.w, p.w, p.g0), p.w);  // B half-step at z_n
   p.z = fma(p.w, h2, p.z);                          // A half-step
-  reflect(m, p.z, p.w, p.S, bad);
+  reflect<R, EX>(m, p.z, p.w, p.S, flag);
 }
-template <typename R>
-__device__ __forceinline__ R baoab_post(const Model<R>& m, R h, R h2, Path<R>& p, bool& bad, R xi) {
+template <typename R, bool EX>
+__device__ __forceinline__ R baoab_post(const Model<R>& m, R h, R h2, Path<R>& p, bool& flag, R xi) {
   R su, lam, g0, g1, e, c;
   profile(m, p.z, su, lam, g0, g1);                 // at z_{n+1/2}
   ou_factors(su, lam, h, e, c);
   p.w = fma(c, xi, e * p.w);                        // O
   p.z = fma(p.w, h2, p.z);                          // A half-step
-  reflect(m, p.z, p.w, p.S, bad);
+  reflect<R, EX>(m, p.z, p.w, p.S, flag);
   drift_coef(m, p.z, p.g0, p.g1);                   // at z_{n+1}
   p.w = fma(h2, fma(p.g1 * p.w, p.w, p.g0), p.w);   // B half-step
   return e;
@@ -262,20 +284,20 @@ __device__ __forceinline__ R baoab_post(const Model<R>& m, R h, R h2, Path<R>& p
 
 // Fine sub-step with normal xi; returns the parity at the noise time (Sn)
 // and the O-step factor e (GL/BAOAB) used by the coarse coupling.
-template <int INTEG, typename R>
+template <int INTEG, typename R, bool EX>
 __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
-                                          bool& bad, R xi, R& Sn, R& e) {
+                                          bool& flag, R xi, R& Sn, R& e) {
   if (INTEG == kSE) {
     Sn = p.S;
     e = R(0);
-    se_step(m, lv.h, p, bad, xi);
+    se_step<R, EX>(m, lv.h, p, flag, xi);
   } else if (INTEG == kGL) {
     Sn = p.S;
-    e = gl_step(m, lv.h, p, bad, xi);
+    e = gl_step<R, EX>(m, lv.h, p, flag, xi);
   } else {
-    baoab_pre(m, lv.h2, p, bad);
+    baoab_pre<R, EX>(m, lv.h2, p, flag);
     Sn = p.S;
-    e = baoab_post(m, lv.h, lv.h2, p, bad, xi);
+    e = baoab_post<R, EX>(m, lv.h, lv.h2, p, flag, xi);
   }
 }
 
@@ -284,23 +306,23 @@ __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv,
 //   SE:       xi_c = S_c (S_a xa + S_b xb) / sqrt(2)          Eq. (euler_coupled_treatment)
 //   GL/BAOAB: xi_c = S_c (ea S_a xa + S_b xb) / sqrt(ea^2 + 1) Eq. (splitting_coupled_treatment)
 // With coupling = 1 (naive) all parities are taken as 1.
-template <int INTEG, typename R>
+template <int INTEG, typename R, bool EX>
 __device__ __forceinline__ void coarse_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
-                                            bool& bad, R xa, R xb, R Sa, R Sb, R ea) {
+                                            bool& flag, R xa, R xb, R Sa, R Sb, R ea) {
   if (m.coupling) { Sa = R(1); Sb = R(1); }
   if (INTEG == kSE) {
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * R(0.70710678118654752440)) * fma(Sa, xa, Sb * xb);
-    se_step(m, lv.hc, p, bad, xc);
+    se_step<R, EX>(m, lv.hc, p, flag, xc);
   } else if (INTEG == kGL) {
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
-    gl_step(m, lv.hc, p, bad, xc);
+    gl_step<R, EX>(m, lv.hc, p, flag, xc);
   } else {
-    baoab_pre(m, lv.hc2, p, bad);
+    baoab_pre<R, EX>(m, lv.hc2, p, flag);
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
-    baoab_post(m, lv.hc, lv.hc2, p, bad, xc);
+    baoab_post<R, EX>(m, lv.hc, lv.hc2, p, flag, xc);
   }
 }
 
@@ -346,10 +368,13 @@ struct Trace {
 // One path pair of a level (Section 3.2): fine path with M steps and, on
 // coupled levels, the coarse path with M/2 steps driven by the same Brownian
 // increments.  Normal n of the fine path is word n mod 4 of Philox block n/4.
+// With EX = false the reflections are the fast single fold and `flag`
+// reports a step that needed more (then the caller replays with EX = true);
+// with EX = true `flag` is the diverged mark.
 // ---------------------------------------------------------------------------
-template <int INTEG, typename R, bool COUPLED, class TR>
-__device__ __forceinline__ void run_pair(const Model<R>& m, const Level<R>& lv, uint64_t i,
-                                         Path<R>& f, Path<R>& c, bool& bad, const TR& tr) {
+template <int INTEG, typename R, bool COUPLED, bool EX, class TR>
+__device__ __forceinline__ void run_pair_impl(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                              Path<R>& f, Path<R>& c, bool& flag, const TR& tr) {
   const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
   const uint32_t w2 = i_hi ^ lv.c2;
   R z0, w0;
@@ -358,63 +383,84 @@ __device__ __forceinline__ void run_pair(const Model<R>& m, const Level<R>& lv, 
   f.g0 = R(0); f.g1 = R(0);
   if (INTEG == kBAOAB) drift_coef(m, z0, f.g0, f.g1);
   c = f;
-  bad = false;
+  flag = false;
   tr.fine(0, f);
   if (COUPLED) tr.coarse(0, c);
   const int64_t M = lv.M;
-  const int64_t nblk = M >> 2;
+  const uint32_t nblk = (uint32_t)(M >> 2);
   R Sa, Sb, ea, eb;
-  for (int64_t b = 0; b < nblk; ++b) {
-    const uint4 x = philox10(m.rk0, m.rk1, (uint32_t)b, i_lo, w2, m.stream_id);
+  for (uint32_t b = 0; b < nblk; ++b) {
+    const uint4 x = philox10(m.rk0, m.rk1, b, i_lo, w2, m.stream_id);
     R xi0, xi1, xi2, xi3;
     box_muller(x.x, x.y, xi0, xi1);
     box_muller(x.z, x.w, xi2, xi3);
+    const int64_t n4 = 4 * (int64_t)b;
     if (COUPLED) {
-      fine_step<INTEG>(m, lv, f, bad, xi0, Sa, ea);
-      tr.fine(4 * b + 1, f);
-      fine_step<INTEG>(m, lv, f, bad, xi1, Sb, eb);
-      tr.fine(4 * b + 2, f);
-      coarse_step<INTEG>(m, lv, c, bad, xi0, xi1, Sa, Sb, ea);
-      tr.coarse(2 * b + 1, c);
-      fine_step<INTEG>(m, lv, f, bad, xi2, Sa, ea);
-      tr.fine(4 * b + 3, f);
-      fine_step<INTEG>(m, lv, f, bad, xi3, Sb, eb);
-      tr.fine(4 * b + 4, f);
-      coarse_step<INTEG>(m, lv, c, bad, xi2, xi3, Sa, Sb, ea);
-      tr.coarse(2 * b + 2, c);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea);
+      tr.fine(n4 + 1, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sb, eb);
+      tr.fine(n4 + 2, f);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi0, xi1, Sa, Sb, ea);
+      tr.coarse(n4 / 2 + 1, c);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea);
+      tr.fine(n4 + 3, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sb, eb);
+      tr.fine(n4 + 4, f);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi2, xi3, Sa, Sb, ea);
+      tr.coarse(n4 / 2 + 2, c);
     } else {
-      fine_step<INTEG>(m, lv, f, bad, xi0, Sa, ea);
-      tr.fine(4 * b + 1, f);
-      fine_step<INTEG>(m, lv, f, bad, xi1, Sa, ea);
-      tr.fine(4 * b + 2, f);
-      fine_step<INTEG>(m, lv, f, bad, xi2, Sa, ea);
-      tr.fine(4 * b + 3, f);
-      fine_step<INTEG>(m, lv, f, bad, xi3, Sa, ea);
-      tr.fine(4 * b + 4, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea);
+      tr.fine(n4 + 1, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sa, ea);
+      tr.fine(n4 + 2, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea);
+      tr.fine(n4 + 3, f);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sa, ea);
+      tr.fine(n4 + 4, f);
     }
   }
   const int tail = (int)(M & 3);  // fine steps left when M is not a multiple of 4
   if (tail) {
-    const uint4 x = philox10(m.rk0, m.rk1, (uint32_t)nblk, i_lo, w2, m.stream_id);
+    const uint4 x = philox10(m.rk0, m.rk1, nblk, i_lo, w2, m.stream_id);
     R xi[4];
     box_muller(x.x, x.y, xi[0], xi[1]);
     box_muller(x.z, x.w, xi[2], xi[3]);
-    const int64_t n0 = 4 * nblk;
+    const int64_t n0 = 4 * (int64_t)nblk;
     if (COUPLED) {
       // M even: tail is 2, one coarse step
-      fine_step<INTEG>(m, lv, f, bad, xi[0], Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[0], Sa, ea);
       tr.fine(n0 + 1, f);
-      fine_step<INTEG>(m, lv, f, bad, xi[1], Sb, eb);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[1], Sb, eb);
       tr.fine(n0 + 2, f);
-      coarse_step<INTEG>(m, lv, c, bad, xi[0], xi[1], Sa, Sb, ea);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi[0], xi[1], Sa, Sb, ea);
       tr.coarse(n0 / 2 + 1, c);
     } else {
       for (int j = 0; j < tail; ++j) {
-        fine_step<INTEG>(m, lv, f, bad, xi[j], Sa, ea);
+        fine_step<INTEG, R, EX>(m, lv, f, flag, xi[j], Sa, ea);
         tr.fine(n0 + j + 1, f);
       }
     }
   }
+}
+
+// A path pair with the diverged mark: the fast pass, replayed exactly (in
+// the rare case a step crossed more than one layer depth).
+template <int INTEG, typename R, bool COUPLED, class TR>
+__device__ __forceinline__ void run_pair(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                         Path<R>& f, Path<R>& c, bool& bad, const TR& tr) {
+  bool multi;
+  run_pair_impl<INTEG, R, COUPLED, false>(m, lv, i, f, c, multi, tr);
+  bad = false;
+  if (multi) run_pair_impl<INTEG, R, COUPLED, true>(m, lv, i, f, c, bad, tr);
+  bad |= !(isfinite(f.z) && isfinite(f.w));
+  if (COUPLED) bad |= !(isfinite(c.z) && isfinite(c.w));
+}
+
+// Always the exact reflection (trace output).
+template <int INTEG, typename R, bool COUPLED, class TR>
+__device__ __forceinline__ void run_pair_exact(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                               Path<R>& f, Path<R>& c, bool& bad, const TR& tr) {
+  run_pair_impl<INTEG, R, COUPLED, true>(m, lv, i, f, c, bad, tr);
   bad |= !(isfinite(f.z) && isfinite(f.w));
   if (COUPLED) bad |= !(isfinite(c.z) && isfinite(c.w));
 }

@@ -45,6 +45,23 @@ struct ReqPlan {
   uint64_t path_steps;
 };
 
+// A request of a device-planned multi-level launch (the graph-driven
+// estimator plans on the device), precision independent, 64 bytes.
+struct PlanReq {
+  int32_t level, coupled;
+  int64_t M;
+  double h;
+  uint64_t first, count, path_steps;
+  uint32_t item_paths, n_items, item_base, pad;
+};
+struct DevPlan {
+  int32_t n_req;
+  uint32_t n_items;
+  uint32_t pad[14];
+  PlanReq req[kMaxReq];
+};
+static_assert(sizeof(PlanReq) == 64, "PlanReq layout");
+
 // Kernel launchers, implemented per precision (prec: 0 float, 1 double).
 cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                               uint64_t N, uint64_t offset, Partial* partials, int grid,
@@ -52,6 +69,9 @@ cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const Le
 cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                               int n_req, uint32_t n_items, Partial* partials,
                               unsigned int* counter, int grid, cudaStream_t st);
+cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, const DevPlan* plan,
+                                  Partial* partials, unsigned int* counter, int grid,
+                                  cudaStream_t st);
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                          uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
                          cudaStream_t st);
@@ -60,9 +80,33 @@ cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSp
 // Resident blocks per SM of the sums / multi-level kernels (occupancy query).
 int blocks_per_sm(int prec, int integ, bool multilevel);
 
+// Device facts, workspace carving and parameter handling (mlmc_api.cu).
+struct DevInfo {
+  int sms = 0, cc = 0;
+};
+// Workspace layout: [256 B header][kMaxReq results][partial slots][graph region].
+constexpr size_t kGraphRegion = 16384;  // device-side MLMC driver state (mlmc_graph.cu)
+struct Workspace {
+  unsigned int* counter;
+  mlmc_level_result* results;
+  Partial* partials;
+  char* graph;
+};
+int device_info(DevInfo* out);
+size_t workspace_needed();
+int carve(void* ws, size_t bytes, Workspace* w);
+int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm);
+int level_spec(const HostModel& hm, int level, LevelSpec* ls);
+uint64_t steps_per_pair(const LevelSpec& ls);
+int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls);
+int grid_for(int prec, int integ, bool multilevel, uint64_t N);
+int cuda_status(cudaError_t e);
+
 // Precision-independent reductions (mlmc_api.cu).
 cudaError_t launch_finalize(const Partial* partials, int nblocks, uint64_t path_steps,
                             mlmc_level_result* d_out, cudaStream_t st);
+cudaError_t launch_finalize_dev(const Partial* partials, const DevPlan* plan,
+                                mlmc_level_result* d_out, cudaStream_t st);
 cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, int n_req,
                                   mlmc_level_result* d_out, cudaStream_t st);
 

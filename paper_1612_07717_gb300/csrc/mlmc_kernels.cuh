@@ -14,6 +14,12 @@
 #include "mlmc_device.cuh"
 #include "mlmc_internal.h"
 
+// Minimum resident blocks per SM requested from the register allocator for
+// the path kernels (1: no register cap).
+#ifndef MLMC_MINB
+#define MLMC_MINB 1
+#endif
+
 namespace mlmc {
 
 // ---------------------------------------------------------------------------
@@ -28,17 +34,18 @@ Model<R> make_model(const HostModel& h) {
   m.Hme = (R)(h.H - h.eps);
   m.invH = (R)(1.0 / h.H);
   m.A = (R)h.A;
-  m.inv_ktau = (R)h.inv_ktau;
+  m.Akt = (R)(h.A * h.inv_ktau);
   m.cfu = (R)h.cfu;
   m.hD = (R)h.hD;
   m.hDs = (R)h.hDs;
+  m.hD_out = h.drift_outside ? (R)h.hD : R(0);
+  m.hDs_out = h.drift_outside ? (R)h.hDs : R(0);
   m.qthr = (R)h.qthr;
   m.z0 = (R)h.z0;
   m.w0 = (R)h.w0;
   m.lim = (R)(1e3 * h.H);
   m.w0_mode = h.w0_mode;
   m.coupling = h.coupling;
-  m.drift_outside = h.drift_outside;
   m.stream_id = h.stream_id;
   for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
   return m;
@@ -60,9 +67,12 @@ Level<R> make_level(const LevelSpec& s) {
 // ---------------------------------------------------------------------------
 // Per-thread accumulator and block reduction
 // ---------------------------------------------------------------------------
+// Per-thread sums are plain FP64 (a thread adds at most a few thousand
+// terms, error below 1e-12 relative); the compensation is applied where the
+// partial sums of a block and of the blocks are combined.  On the coarsest
+// level P_c = 0, so only sum Y and sum Y^2 are kept (sum P_f = sum Y).
 struct Acc {
-  double y, cy, y2, cy2;   // Kahan pairs: sum Y, sum Y^2 of QoI 0
-  double pf, pf2, pc, pc2;
+  double y, y2, pf, pf2, pc, pc2;
   uint32_t n, bad, nf, nc, nd;
 };
 
@@ -74,34 +84,43 @@ __device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
 }
 
 __device__ __forceinline__ void acc_zero(Acc& a) {
-  a.y = a.cy = a.y2 = a.cy2 = a.pf = a.pf2 = a.pc = a.pc2 = 0.0;
+  a.y = a.y2 = a.pf = a.pf2 = a.pc = a.pc2 = 0.0;
   a.n = a.bad = a.nf = a.nc = a.nd = 0;
 }
 
-// QoIs at T (Section 3.2): P = z(T) and P = 1[z(T) < threshold]; the
-// indicator decision is taken in the path precision.
+// QoIs at T (Section 3.2): P = z(T) and P = 1[z(T) < threshold]; Y = P_f -
+// P_c is formed in FP64 (exact for two floats); the indicator decision is
+// taken in the path precision.
 template <typename R, bool COUPLED>
 __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, bool bad) {
   if (bad) { a.bad += 1; return; }
   const double Pf = (double)zf;
-  const double Pc = COUPLED ? (double)zc : 0.0;
-  const double Y = Pf - Pc;
-  kahan_add(a.y, a.cy, Y);
-  kahan_add(a.y2, a.cy2, Y * Y);
-  a.pf += Pf; a.pf2 += Pf * Pf;
-  a.pc += Pc; a.pc2 += Pc * Pc;
+  if (COUPLED) {
+    const double Pc = (double)zc;
+    const double Y = Pf - Pc;
+    a.y += Y;
+    a.y2 = fma(Y, Y, a.y2);
+    a.pf += Pf;
+    a.pf2 = fma(Pf, Pf, a.pf2);
+    a.pc += Pc;
+    a.pc2 = fma(Pc, Pc, a.pc2);
+  } else {
+    a.y += Pf;
+    a.y2 = fma(Pf, Pf, a.y2);
+  }
   const bool If = zf < m.qthr;
   const bool Ic = COUPLED && (zc < m.qthr);
   a.nf += If; a.nc += Ic; a.nd += (If != Ic);
   a.n += 1;
 }
 
-// Warp tree (fixed order), then warp 0's lane 0 adds the warp results in
+// Warp tree (fixed order), then lane 0 of warp 0 adds the warp results in
 // warp order with Kahan compensation.  Ends with the block synchronised.
-__device__ __forceinline__ void block_reduce_store(const Acc& a, Partial* __restrict__ out) {
+__device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled,
+                                                   Partial* __restrict__ out) {
   __shared__ double s_v[kBlock / 32][6];
   __shared__ unsigned long long s_u[kBlock / 32][5];
-  double v[6] = {a.y - a.cy, a.y2 - a.cy2, a.pf, a.pf2, a.pc, a.pc2};
+  double v[6] = {a.y, a.y2, coupled ? a.pf : a.y, coupled ? a.pf2 : a.y2, a.pc, a.pc2};
   unsigned long long u[5] = {a.n, a.bad, a.nf, a.nc, a.nd};
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -144,7 +163,7 @@ struct SumsArgs {
 };
 
 template <int INTEG, typename R, bool COUPLED>
-__global__ void __launch_bounds__(kBlock) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
   Acc acc;
   acc_zero(acc);
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
@@ -154,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_level_sums(const __grid_constant__ S
     run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
     acc_add<R, COUPLED>(acc, a.m, f.z, c.z, bad);
   }
-  block_reduce_store(acc, a.partials + blockIdx.x);
+  block_reduce_store(acc, COUPLED, a.partials + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,18 +197,18 @@ struct MultiArgs {
 };
 
 template <int INTEG, typename R, bool COUPLED>
-__device__ __forceinline__ void multilevel_item(const Model<R>& m, const ReqDev<R>& rq,
+__device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
                                                 uint64_t first, uint32_t count, Acc& acc) {
   for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
     Path<R> f, c;
     bool bad;
-    run_pair<INTEG, R, COUPLED>(m, rq.lv, first + j, f, c, bad, NoTrace<R>());
+    run_pair<INTEG, R, COUPLED>(m, lv, first + j, f, c, bad, NoTrace<R>());
     acc_add<R, COUPLED>(acc, m, f.z, c.z, bad);
   }
 }
 
 template <int INTEG, typename R>
-__global__ void __launch_bounds__(kBlock) k_multilevel(const __grid_constant__ MultiArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel(const __grid_constant__ MultiArgs<R> a) {
   __shared__ unsigned int s_item;
   // Every block does at most n_items iterations: the loop ends when the
   // shared counter passes the last item; there is no waiting on other blocks.
@@ -208,11 +227,56 @@ __global__ void __launch_bounds__(kBlock) k_multilevel(const __grid_constant__ M
     const uint32_t count = (uint32_t)(left < rq.item_paths ? left : rq.item_paths);
     Acc acc;
     acc_zero(acc);
-    if (rq.lv.coupled)
-      multilevel_item<INTEG, R, true>(a.m, rq, rq.first + start, count, acc);
+    const Level<R> lv = rq.lv;   // registers, not parameter-space loads per step
+    if (lv.coupled)
+      multilevel_item<INTEG, R, true>(a.m, lv, rq.first + start, count, acc);
     else
-      multilevel_item<INTEG, R, false>(a.m, rq, rq.first + start, count, acc);
-    block_reduce_store(acc, a.partials + it);
+      multilevel_item<INTEG, R, false>(a.m, lv, rq.first + start, count, acc);
+    block_reduce_store(acc, lv.coupled != 0, a.partials + it);
+  }
+}
+
+// The same persistent kernel with its plan in device memory (written by the
+// device-side MLMC driver between launches of a captured graph).
+template <int INTEG, typename R>
+__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __grid_constant__ Model<R> m,
+                                                           const DevPlan* __restrict__ plan,
+                                                           Partial* __restrict__ partials,
+                                                           unsigned int* __restrict__ counter) {
+  __shared__ unsigned int s_item;
+  const int n_req = plan->n_req;
+  const uint32_t n_items = plan->n_items;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const unsigned int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    int r = 0;
+    while (r + 1 < n_req && it >= plan->req[r + 1].item_base) ++r;
+    const PlanReq& pr = plan->req[r];
+    ReqDev<R> rq;
+    rq.lv.h = (R)pr.h;
+    rq.lv.h2 = (R)(0.5 * pr.h);
+    rq.lv.hc = (R)(2.0 * pr.h);
+    rq.lv.hc2 = (R)pr.h;
+    rq.lv.M = pr.M;
+    rq.lv.c2 = (uint32_t)pr.level << 24;
+    rq.lv.coupled = pr.coupled;
+    rq.first = pr.first;
+    rq.count = pr.count;
+    rq.item_paths = pr.item_paths;
+    const uint32_t local = it - pr.item_base;
+    const uint64_t start = (uint64_t)local * pr.item_paths;
+    const uint64_t left = pr.count - start;
+    const uint32_t count = (uint32_t)(left < pr.item_paths ? left : pr.item_paths);
+    Acc acc;
+    acc_zero(acc);
+    if (pr.coupled)
+      multilevel_item<INTEG, R, true>(m, rq.lv, pr.first + start, count, acc);
+    else
+      multilevel_item<INTEG, R, false>(m, rq.lv, pr.first + start, count, acc);
+    block_reduce_store(acc, pr.coupled != 0, partials + it);
   }
 }
 
@@ -254,7 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ PathsA
   tr.c = (COUPLED && a.tc) ? a.tc + (uint64_t)3 * (M / 2 + 1) * j : nullptr;
   Path<R> f, c;
   bool bad;
-  run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, tr);
+  run_pair_exact<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, tr);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,6 +389,17 @@ cudaError_t multilevel_impl(int integ, const HostModel& hm, const ReqPlan* plan,
   if (integ == kSE) k_multilevel<kSE, R><<<grid, kBlock, 0, st>>>(a);
   else if (integ == kGL) k_multilevel<kGL, R><<<grid, kBlock, 0, st>>>(a);
   else k_multilevel<kBAOAB, R><<<grid, kBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t multilevel_dev_impl(int integ, const HostModel& hm, const DevPlan* plan,
+                                Partial* partials, unsigned int* counter, int grid,
+                                cudaStream_t st) {
+  const Model<R> m = make_model<R>(hm);
+  if (integ == kSE) k_multilevel_dev<kSE, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
+  else if (integ == kGL) k_multilevel_dev<kGL, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
+  else k_multilevel_dev<kBAOAB, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,10 @@ cudaError_t multilevel(int integ, const HostModel& hm, const ReqPlan* plan, int 
                        cudaStream_t st) {
   return multilevel_impl<float>(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
 }
+cudaError_t multilevel_dev(int integ, const HostModel& hm, const DevPlan* plan, Partial* partials,
+                           unsigned int* counter, int grid, cudaStream_t st) {
+  return multilevel_dev_impl<float>(integ, hm, plan, partials, counter, grid, st);
+}
 cudaError_t paths(int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N, uint64_t offset,
                   void* states, int32_t* flags, void* tf, void* tc, bool trace, cudaStream_t st) {
   return paths_impl<float>(integ, hm, lv, N, offset, states, flags, tf, tc, trace, st);
