@@ -19,6 +19,9 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libmlmc.so")
 SOURCES = ["mlmc_api.cu", "mlmc_graph.cu", "mlmc_kernels_f32.cu", "mlmc_kernels_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 path kernels flush subnormals (no value of the path is subnormal
+# except an exp(-lambda h) that underflows, which is then 0).
+FLAGS = {"mlmc_kernels_f32.cu": ["-ftz=true"]}
 
 
 def nvcc_path():
@@ -54,7 +57,8 @@ def build(force=False, verbose=False, ptxas_info=False):
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        extra = FLAGS.get(src, [])
+        cmd = [nvcc] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

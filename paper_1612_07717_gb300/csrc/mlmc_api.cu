@@ -11,6 +11,10 @@
 namespace mlmc {
 
 namespace prec_f32 {
+cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,
+                             unsigned int*, int, cudaStream_t);
+size_t model_size();
+void model_image(const HostModel&, void*);
 cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
                            cudaStream_t);
 cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
@@ -22,6 +26,10 @@ cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, v
 int occupancy(int, bool);
 }  // namespace prec_f32
 namespace prec_f64 {
+cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,
+                             unsigned int*, int, cudaStream_t);
+size_t model_size();
+void model_image(const HostModel&, void*);
 cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
                            cudaStream_t);
 cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
@@ -50,6 +58,19 @@ cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, cons
                                   cudaStream_t st) {
   return prec ? prec_f64::multilevel_dev(integ, hm, plan, partials, counter, grid, st)
               : prec_f32::multilevel_dev(integ, hm, plan, partials, counter, grid, st);
+}
+cudaError_t launch_multilevel_table(int prec, int integ, const void* models, const PlanReq* reqs,
+                                   int n_req, uint32_t n_items, Partial* partials,
+                                   unsigned int* counter, int grid, cudaStream_t st) {
+  return prec ? prec_f64::multilevel_table(integ, models, reqs, n_req, n_items, partials, counter,
+                                           grid, st)
+              : prec_f32::multilevel_table(integ, models, reqs, n_req, n_items, partials, counter,
+                                           grid, st);
+}
+size_t model_bytes(int prec) { return prec ? prec_f64::model_size() : prec_f32::model_size(); }
+void model_image(int prec, const HostModel& hm, void* out) {
+  if (prec) prec_f64::model_image(hm, out);
+  else prec_f32::model_image(hm, out);
 }
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                          uint64_t offset, void* s, int32_t* f, cudaStream_t st) {
@@ -152,6 +173,21 @@ __global__ void __launch_bounds__(kBlock) k_finalize_dev(const Partial* __restri
 cudaError_t launch_finalize_dev(const Partial* partials, const DevPlan* plan,
                                 mlmc_level_result* d_out, cudaStream_t st) {
   k_finalize_dev<<<kMaxReq, kBlock, 0, st>>>(partials, plan, d_out);
+  return cudaGetLastError();
+}
+
+// Reduction of a request table: one block per request.
+__global__ void __launch_bounds__(kBlock) k_finalize_table(const Partial* __restrict__ p,
+                                                           const PlanReq* __restrict__ reqs,
+                                                           mlmc_level_result* __restrict__ out) {
+  const PlanReq& q = reqs[blockIdx.x];
+  reduce_range(p, q.item_base, q.item_base + q.n_items, q.path_steps, out + blockIdx.x);
+}
+
+cudaError_t launch_finalize_table(const Partial* partials, const PlanReq* reqs, int n_req,
+                                  mlmc_level_result* d_out, cudaStream_t st) {
+  if (n_req <= 0) return cudaSuccess;
+  k_finalize_table<<<n_req, kBlock, 0, st>>>(partials, reqs, d_out);
   return cudaGetLastError();
 }
 

@@ -43,43 +43,84 @@ template <typename R>
 struct Level {
   R h, h2;            // fine step h and h / 2
   R hc, hc2;          // coarse step 2h and h
+  R hl2, hcl2;        // h log2(e) and 2h log2(e) (arguments of the base-2 exponential)
   int64_t M;          // fine steps
   uint32_t c2;        // level word xored into counter word 2: level << 24
   int32_t coupled;    // 0 on the coarsest level
 };
 
 // ---------------------------------------------------------------------------
-// Precision-generic primitives.  The float versions use the SFU (MUFU)
-// approximations; the double versions the IEEE routines.
+// Precision-generic primitives.  Float: single SFU instructions through the
+// PTX approximations with flush-to-zero (the kernels never see subnormal
+// values that matter: the smallest is exp(-lambda h) underflowing to 0).
+// Double: the IEEE routines.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float ptx_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_sin(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_cos(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float rsqrt_(float x) { return ptx_rsqrt(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp_(float x) { return ptx_rcp(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ float sqrt_(float x) { return x * ptx_rsqrt(x); }  // x > 0
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float expneg_(float x) { return __expf(-x); }
-__device__ __forceinline__ double expneg_(double x) { return exp(-x); }
 __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
 
-// 1 - exp(-2x) for x >= 0 given e = exp(-x), without cancellation at small
-// x.  Float: Taylor series of 1 - e^{-2x} through x^5 below x = 0.05
-// (truncation < 1.5e-8 relative), 1 - e*e above (cancellation < 7e-7
-// relative).  Double: expm1.
-__device__ __forceinline__ float one_minus_e2(float x, float e) {
-  float s = 4.0f / 15.0f;
-  s = fmaf(s, x, -2.0f / 3.0f);
-  s = fmaf(s, x, 4.0f / 3.0f);
-  s = fmaf(s, x, -2.0f);
-  s = fmaf(s, x, 2.0f);
-  const float series = s * x;
+// O-step factors from y = lambda h log2(e) (the argument of the base-2
+// exponential): e = exp(-lambda h) = 2^-y and 1 - e^2 = 1 - exp(-2 lambda h)
+// without cancellation at small y.  Float: Taylor series of
+// 1 - 2^{-2y} = 1 - e^{-2 y ln 2} through y^5 below y = 0.07 (truncation
+// below 1.5e-8 relative), 1 - e*e above (cancellation below 5e-7 relative).
+// Double: exp and expm1 of lambda h.
+constexpr float kLn2 = 0.69314718055994530942f;
+__device__ __forceinline__ void exp_pair(float y, float& e, float& om) {
+  e = ptx_ex2(-y);
+  const float a = 2.0f * kLn2;                       // 1 - e^{-a y} = a y - (a y)^2/2 + ...
+  float s = a * a * a * a * a / 120.0f;
+  s = fmaf(s, -y, a * a * a * a / 24.0f);
+  s = fmaf(s, -y, a * a * a / 6.0f);
+  s = fmaf(s, -y, a * a / 2.0f);
+  s = fmaf(s, -y, a);
+  const float series = s * y;
   const float direct = fmaf(-e, e, 1.0f);
-  return x < 0.05f ? series : direct;
+  om = y < 0.07f ? series : direct;
 }
-__device__ __forceinline__ double one_minus_e2(double x, double) { return -expm1(-2.0 * x); }
+__device__ __forceinline__ void exp_pair(double y, double& e, double& om) {
+  const double x = y * 0.69314718055994530942;
+  e = exp(-x);
+  om = -expm1(-2.0 * x);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys of the
@@ -114,15 +155,15 @@ __device__ __forceinline__ double u01d(uint32_t x) {
 
 // Box-Muller on a word pair: R = sqrt(-2 ln u_a), angle 2 pi u_b.  The
 // float path evaluates the angle as 2 pi (u_b - 1/2) in (-pi, pi), where the
-// SFU sine and cosine are accurate, and negates (cos(t + pi) = -cos t).
+// SFU sine and cosine are accurate, and negates (cos(t + pi) = -cos t);
+// -2 ln u = -2 ln(2) log2(u).
 __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& na, float& nb) {
   const float ua = u01f(xa), ub = u01f(xb);
-  const float s2 = -2.0f * __logf(ua);
-  const float r = s2 * rsqrtf(s2);
-  float sn, cs;
-  __sincosf(6.28318530717958647692f * (ub - 0.5f), &sn, &cs);
-  na = -r * cs;
-  nb = -r * sn;
+  const float s2 = (-2.0f * kLn2) * ptx_lg2(ua);
+  const float r = s2 * ptx_rsqrt(s2);
+  const float t = 6.28318530717958647692f * (ub - 0.5f);
+  na = -r * ptx_cos(t);
+  nb = -r * ptx_sin(t);
 }
 __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& na, double& nb) {
   const double ua = u01d(xa), ub = u01d(xb);
@@ -179,22 +220,22 @@ __device__ __forceinline__ void drift_coef(const Model<R>& m, R z, R& g0, R& g1)
 //
 // reflect_fast: one reflection, branch-free and exact: z' = min(|z|, 2H - |z|)
 // equals z inside [0, H], -z below, 2H - z above; a reflection happened iff
-// z' != z.  It equals the oracle's fold for z in [-H, 2H]; outside that range
-// (more than one reflection) it sets the sticky `multi` flag, and the caller
-// replays the whole path with reflect_exact.  (Steps that cross more than one layer depth only occur on
-// paths that are diverging.)
+// z' != z.  It equals the oracle's fold whenever the unfolded z lies in
+// [-H, 2H], which holds when the A-step displacement |w| h_A is at most H
+// (z starts every A-step inside [0, H]).  The path keeps the largest |w|
+// entering an A-step; if |w|max h_A > H the caller replays the whole path
+// with reflect_exact.  (Such steps only occur on paths that are diverging.)
 //
 // reflect_exact: the loop of single reflections, as in the oracle, with
 // |z| > 1e3 H (or NaN) marking the path as diverged.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void reflect_fast(const Model<R>& m, R& z, R& w, R& S, bool& multi) {
+__device__ __forceinline__ void reflect_fast(const Model<R>& m, R& z, R& w, R& S) {
   const R za = fabs(z);
   const R zr = fmin_(za, m.twoH - za);
   const bool flip = zr != z;
   w = flip ? -w : w;
   S = flip ? -S : S;
-  multi |= (z < -m.H) | (zr < R(0));  // exact tests of z outside [-H, 2H]
   z = zr;
 }
 
@@ -211,7 +252,7 @@ __device__ __forceinline__ void reflect_exact(const Model<R>& m, R& z, R& w, R& 
 template <typename R, bool EXACT>
 __device__ __forceinline__ void reflect(const Model<R>& m, R& z, R& w, R& S, bool& flag) {
   if (EXACT) reflect_exact(m, z, w, S, flag);
-  else reflect_fast(m, z, w, S, flag);
+  else reflect_fast(m, z, w, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +263,7 @@ template <typename R>
 struct Path {
   R z, w, S;
   R g0, g1;
+  R wm;     // largest |w| entering an A-step
 };
 
 // Symplectic Euler, Eq. (MethodSymplecticEuler):
@@ -234,27 +276,30 @@ __device__ __forceinline__ void se_step(const Model<R>& m, R h, Path<R>& p, bool
   const R amp = su * sqrt_((R(2) * h) * lam);
   const R acc = fma(-lam, p.w, fma(g1 * p.w, p.w, g0));
   p.w = fma(amp, xi, fma(h, acc, p.w));
+  p.wm = fmax_(p.wm, fabs(p.w));
   p.z = fma(p.w, h, p.z);
   reflect<R, EX>(m, p.z, p.w, p.S, flag);
 }
 
 // O-step factors: e = exp(-lambda h) and the noise amplitude
-// sigma sqrt((1 - e^{-2 lambda h}) / (2 lambda)) = sigma_w sqrt(1 - e^2).
+// sigma sqrt((1 - e^{-2 lambda h}) / (2 lambda)) = sigma_w sqrt(1 - e^2);
+// hl2 = h log2(e).
 template <typename R>
-__device__ __forceinline__ void ou_factors(R su, R lam, R h, R& e, R& c) {
-  const R x = lam * h;
-  e = expneg_(x);
-  c = su * sqrt_(one_minus_e2(x, e));
+__device__ __forceinline__ void ou_factors(R su, R lam, R hl2, R& e, R& c) {
+  R om;
+  exp_pair(lam * hl2, e, om);
+  c = su * sqrt_(om);
 }
 
 // Geometric Langevin (OBA), Eq. (MethodSymplecticEulerOU).  Returns e.
 template <typename R, bool EX>
-__device__ __forceinline__ R gl_step(const Model<R>& m, R h, Path<R>& p, bool& flag, R xi) {
+__device__ __forceinline__ R gl_step(const Model<R>& m, R h, R hl2, Path<R>& p, bool& flag, R xi) {
   R su, lam, g0, g1, e, c;
   profile(m, p.z, su, lam, g0, g1);
-  ou_factors(su, lam, h, e, c);
+  ou_factors(su, lam, hl2, e, c);
   const R us = fma(c, xi, e * p.w);          // O
   p.w = fma(h, fma(g1 * us, us, g0), us);    // B at (z_n, u*)
+  p.wm = fmax_(p.wm, fabs(p.w));
   p.z = fma(p.w, h, p.z);                    // A
   reflect<R, EX>(m, p.z, p.w, p.S, flag);
   return e;
@@ -266,15 +311,18 @@ __device__ __forceinline__ R gl_step(const Model<R>& m, R h, Path<R>& p, bool& f
 template <typename R, bool EX>
 __device__ __forceinline__ void baoab_pre(const Model<R>& m, R h2, Path<R>& p, bool& flag) {
   p.w = fma(h2, fma(p.g1 * p.w, p.w, p.g0), p.w);  // B half-step at z_n
+  p.wm = fmax_(p.wm, fabs(p.w));
   p.z = fma(p.w, h2, p.z);                          // A half-step
   reflect<R, EX>(m, p.z, p.w, p.S, flag);
 }
 template <typename R, bool EX>
-__device__ __forceinline__ R baoab_post(const Model<R>& m, R h, R h2, Path<R>& p, bool& flag, R xi) {
+__device__ __forceinline__ R baoab_post(const Model<R>& m, R hl2, R h2, Path<R>& p, bool& flag,
+                                        R xi) {
   R su, lam, g0, g1, e, c;
   profile(m, p.z, su, lam, g0, g1);                 // at z_{n+1/2}
-  ou_factors(su, lam, h, e, c);
+  ou_factors(su, lam, hl2, e, c);
   p.w = fma(c, xi, e * p.w);                        // O
+  p.wm = fmax_(p.wm, fabs(p.w));
   p.z = fma(p.w, h2, p.z);                          // A half-step
   reflect<R, EX>(m, p.z, p.w, p.S, flag);
   drift_coef(m, p.z, p.g0, p.g1);                   // at z_{n+1}
@@ -293,11 +341,11 @@ __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv,
     se_step<R, EX>(m, lv.h, p, flag, xi);
   } else if (INTEG == kGL) {
     Sn = p.S;
-    e = gl_step<R, EX>(m, lv.h, p, flag, xi);
+    e = gl_step<R, EX>(m, lv.h, lv.hl2, p, flag, xi);
   } else {
     baoab_pre<R, EX>(m, lv.h2, p, flag);
     Sn = p.S;
-    e = baoab_post<R, EX>(m, lv.h, lv.h2, p, flag, xi);
+    e = baoab_post<R, EX>(m, lv.hl2, lv.h2, p, flag, xi);
   }
 }
 
@@ -317,12 +365,12 @@ __device__ __forceinline__ void coarse_step(const Model<R>& m, const Level<R>& l
   } else if (INTEG == kGL) {
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
-    gl_step<R, EX>(m, lv.hc, p, flag, xc);
+    gl_step<R, EX>(m, lv.hc, lv.hcl2, p, flag, xc);
   } else {
     baoab_pre<R, EX>(m, lv.hc2, p, flag);
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
-    baoab_post<R, EX>(m, lv.hc, lv.hc2, p, flag, xc);
+    baoab_post<R, EX>(m, lv.hcl2, lv.hc2, p, flag, xc);
   }
 }
 
@@ -381,6 +429,7 @@ __device__ __forceinline__ void run_pair_impl(const Model<R>& m, const Level<R>&
   initial_state(m, lv, i_lo, i_hi, z0, w0);
   f.z = z0; f.w = w0; f.S = R(1);
   f.g0 = R(0); f.g1 = R(0);
+  f.wm = R(0);
   if (INTEG == kBAOAB) drift_coef(m, z0, f.g0, f.g1);
   c = f;
   flag = false;
@@ -440,6 +489,13 @@ __device__ __forceinline__ void run_pair_impl(const Model<R>& m, const Level<R>&
         tr.fine(n0 + j + 1, f);
       }
     }
+  }
+  if (!EX) {
+    // a single fold per A-step is exact while |w| h_A <= H (see reflect_fast)
+    const R hA = INTEG == kBAOAB ? lv.h2 : lv.h;
+    const R hAc = INTEG == kBAOAB ? lv.hc2 : lv.hc;
+    flag = f.wm * hA > m.H;
+    if (COUPLED) flag |= c.wm * hAc > m.H;
   }
 }
 

@@ -68,7 +68,7 @@ __device__ void plan_device(const GState* g, DevPlan* plan) {
       q.item_paths = (uint32_t)item_paths;
       q.n_items = (uint32_t)n_it;
       q.item_base = (uint32_t)items;
-      q.pad = 0;
+      q.slot = 0;
       items += n_it;
     }
     plan->n_req = k;

@@ -52,7 +52,7 @@ struct PlanReq {
   int64_t M;
   double h;
   uint64_t first, count, path_steps;
-  uint32_t item_paths, n_items, item_base, pad;
+  uint32_t item_paths, n_items, item_base, slot;  // slot: query of a multi-query batch
 };
 struct DevPlan {
   int32_t n_req;
@@ -72,6 +72,14 @@ cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const Re
 cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, const DevPlan* plan,
                                   Partial* partials, unsigned int* counter, int grid,
                                   cudaStream_t st);
+// Multi-query batches (serving): a table of requests in device memory, each
+// tagged with the slot of its query's Model in a device array of Models.
+cudaError_t launch_multilevel_table(int prec, int integ, const void* models, const PlanReq* reqs,
+                                   int n_req, uint32_t n_items, Partial* partials,
+                                   unsigned int* counter, int grid, cudaStream_t st);
+// Bytes of one device Model of precision prec, and its host image.
+size_t model_bytes(int prec);
+void model_image(int prec, const HostModel& hm, void* out);
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                          uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
                          cudaStream_t st);
@@ -107,6 +115,8 @@ cudaError_t launch_finalize(const Partial* partials, int nblocks, uint64_t path_
                             mlmc_level_result* d_out, cudaStream_t st);
 cudaError_t launch_finalize_dev(const Partial* partials, const DevPlan* plan,
                                 mlmc_level_result* d_out, cudaStream_t st);
+cudaError_t launch_finalize_table(const Partial* partials, const PlanReq* reqs, int n_req,
+                                  mlmc_level_result* d_out, cudaStream_t st);
 cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, int n_req,
                                   mlmc_level_result* d_out, cudaStream_t st);
 

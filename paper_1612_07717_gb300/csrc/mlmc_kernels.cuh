@@ -58,6 +58,8 @@ Level<R> make_level(const LevelSpec& s) {
   l.h2 = (R)(0.5 * s.h);
   l.hc = (R)(2.0 * s.h);
   l.hc2 = (R)s.h;
+  l.hl2 = (R)(s.h * 1.4426950408889634074);
+  l.hcl2 = (R)(2.0 * s.h * 1.4426950408889634074);
   l.M = s.M;
   l.c2 = (uint32_t)s.level << 24;
   l.coupled = s.coupled ? 1 : 0;
@@ -260,12 +262,15 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
     rq.lv.h2 = (R)(0.5 * pr.h);
     rq.lv.hc = (R)(2.0 * pr.h);
     rq.lv.hc2 = (R)pr.h;
+    rq.lv.hl2 = (R)(pr.h * 1.4426950408889634074);
+    rq.lv.hcl2 = (R)(2.0 * pr.h * 1.4426950408889634074);
     rq.lv.M = pr.M;
     rq.lv.c2 = (uint32_t)pr.level << 24;
     rq.lv.coupled = pr.coupled;
     rq.first = pr.first;
     rq.count = pr.count;
     rq.item_paths = pr.item_paths;
+    rq.pad = 0;
     const uint32_t local = it - pr.item_base;
     const uint64_t start = (uint64_t)local * pr.item_paths;
     const uint64_t left = pr.count - start;
@@ -276,6 +281,60 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
       multilevel_item<INTEG, R, true>(m, rq.lv, pr.first + start, count, acc);
     else
       multilevel_item<INTEG, R, false>(m, rq.lv, pr.first + start, count, acc);
+    block_reduce_store(acc, pr.coupled != 0, partials + it);
+  }
+}
+
+// Multi-query batches: the request table lives in device memory and each
+// request names the slot of its query's Model.  Items of different queries
+// share one launch; each request's items are reduced in item order, and the
+// item split of a request does not depend on the rest of the batch, so a
+// query's sums are the same alone and in any mix.
+template <int INTEG, typename R>
+__global__ void __launch_bounds__(kBlock, MLMC_MINB)
+    k_multilevel_table(const Model<R>* __restrict__ models, const PlanReq* __restrict__ reqs,
+                       int n_req, uint32_t n_items, Partial* __restrict__ partials,
+                       unsigned int* __restrict__ counter) {
+  __shared__ unsigned int s_item;
+  __shared__ int s_req;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned int it = atomicAdd(counter, 1u);
+      int lo = 0, hi = n_req - 1;                    // last request with item_base <= it
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].item_base <= it) lo = mid; else hi = mid - 1;
+      }
+      s_item = it;
+      s_req = lo;
+    }
+    __syncthreads();
+    const unsigned int it = s_item;
+    const int r = s_req;
+    __syncthreads();
+    if (it >= n_items) break;
+    const PlanReq pr = reqs[r];
+    const Model<R> m = models[pr.slot];
+    Level<R> lv;
+    lv.h = (R)pr.h;
+    lv.h2 = (R)(0.5 * pr.h);
+    lv.hc = (R)(2.0 * pr.h);
+    lv.hc2 = (R)pr.h;
+    lv.hl2 = (R)(pr.h * 1.4426950408889634074);
+    lv.hcl2 = (R)(2.0 * pr.h * 1.4426950408889634074);
+    lv.M = pr.M;
+    lv.c2 = (uint32_t)pr.level << 24;
+    lv.coupled = pr.coupled;
+    const uint32_t local = it - pr.item_base;
+    const uint64_t start = (uint64_t)local * pr.item_paths;
+    const uint64_t left = pr.count - start;
+    const uint32_t count = (uint32_t)(left < pr.item_paths ? left : pr.item_paths);
+    Acc acc;
+    acc_zero(acc);
+    if (pr.coupled)
+      multilevel_item<INTEG, R, true>(m, lv, pr.first + start, count, acc);
+    else
+      multilevel_item<INTEG, R, false>(m, lv, pr.first + start, count, acc);
     block_reduce_store(acc, pr.coupled != 0, partials + it);
   }
 }
@@ -400,6 +459,20 @@ cudaError_t multilevel_dev_impl(int integ, const HostModel& hm, const DevPlan* p
   if (integ == kSE) k_multilevel_dev<kSE, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
   else if (integ == kGL) k_multilevel_dev<kGL, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
   else k_multilevel_dev<kBAOAB, R><<<grid, kBlock, 0, st>>>(m, plan, partials, counter);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t multilevel_table_impl(int integ, const void* models, const PlanReq* reqs, int n_req,
+                                  uint32_t n_items, Partial* partials, unsigned int* counter,
+                                  int grid, cudaStream_t st) {
+  const Model<R>* mm = (const Model<R>*)models;
+  if (integ == kSE)
+    k_multilevel_table<kSE, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
+  else if (integ == kGL)
+    k_multilevel_table<kGL, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
+  else
+    k_multilevel_table<kBAOAB, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
   return cudaGetLastError();
 }
 
