@@ -160,6 +160,45 @@ def cpu_baseline_sample():
                       % (ORACLE_SAMPLE_SCALE, steps, dt)}
 
 
+def time_to_eps(G, W, torch, eps_frac=2.0 ** -10):
+    """Wall time to RMSE eps = H * eps_frac on mean z(T): MLMC with FP32
+    BAOAB paths (the adaptive loop as one CUDA graph) against plain Monte
+    Carlo with FP64 symplectic-Euler paths at the timestep the SE hierarchy
+    needs for the same eps (its finest level)."""
+    H = W.BL600["H"]
+    eps = H * eps_frac
+    out = {"eps_m": eps}
+    pb = G.make_params(W.bl600(G.BAOAB, L_max=14, n_init=10000), precision=G.FP32)
+    ws = G.Workspace(pb)
+    ge = G.GraphEstimator(eps, G.BAOAB, pb, 3, workspace=ws)
+    ge.launch(); ge.result()                        # warm-up (module load, first launch)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ge.launch()
+    r = ge.result()
+    dt = time.perf_counter() - t
+    ge.close()
+    out["mlmc_fp32_baoab_graph"] = {"seconds": dt, "L": r["L"], "estimate_m": r["estimate"][0],
+                                    "rmse_stat_m": math.sqrt(r["est_variance"][0]),
+                                    "path_steps": r["total_path_steps"], "N": r["N"],
+                                    "converged": r["converged"]}
+    # the SE hierarchy's finest level for this eps sets the plain-MC timestep
+    pse = G.make_params(W.bl600(G.SE, L_max=16, n_init=10000), precision=G.FP32)
+    rse = G.estimate_graph(eps, G.SE, pse, 5, workspace=ws)
+    level = rse["L"]
+    p64 = G.make_params(W.bl600(G.SE), precision=G.FP64, level_min=level)
+    t = time.perf_counter()
+    s = G.stmc_estimate(eps, level, G.SE, p64, 7, n_pilot=4000, workspace=ws)
+    dt64 = time.perf_counter() - t
+    out["stmc_fp64_se"] = {"seconds": dt64, "level": level, "M": 8 << level,
+                           "N": s["N"][0], "estimate_m": s["estimate"][0],
+                           "rmse_stat_m": math.sqrt(s["est_variance"][0]),
+                           "path_steps": s["total_path_steps"]}
+    out["mlmc_fp32_se_graph_level"] = level
+    out["speedup"] = dt64 / dt if dt > 0 else None
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +206,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-eps", action="store_true")
     ap.add_argument("--n0", type=float, default=N0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -185,7 +225,12 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_1612_07717_gb300 as G
+    from paper_1612_07717_gb300 import autotune
     from paper_1612_07717_gb300 import workloads as W
+
+    tuned = autotune.apply()            # the autotuner's table for this GPU, if recorded
+    tuning = dict(autotune.get_tuning(INTEGRATOR, G.FP32),
+                  source="autotuner table" if tuned else "library defaults")
 
     # each rank takes its own slice of every level's path range (weak scaling:
     # the per-GPU work is the full schedule; ranks use disjoint path indices)
@@ -263,6 +308,7 @@ def main():
                        "path_steps_per_step": steps_per_step, "integrator": "BAOAB",
                        "paths": "fp32", "sums": "fp64 Kahan",
                        "l2": "flushed between timed steps (256 MB write)",
+                       "tuning": tuning,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
@@ -275,6 +321,8 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if not args.no_time_to_eps:
+            out["time_to_eps"] = time_to_eps(G, W, torch)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(out))

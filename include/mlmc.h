@@ -145,6 +145,21 @@ const char* mlmc_strerror(int code);
  * device is visible. */
 int mlmc_device_info(int32_t out[3]);
 
+/* Tuning of the persistent multi-level kernels for one (integrator,
+ * precision): `variant` is the register budget the kernel was compiled for,
+ * as resident blocks per SM (1 uncapped, 3, or 4; FP64 only 1);
+ * `items_per_block` the planner's work items per resident block (1..1024;
+ * smaller items balance better, larger ones reduce per-item overhead);
+ * `blocks_per_sm` the resident blocks per SM launched (0 = all that fit).
+ * The table is process-wide; the library starts from GB300-measured
+ * defaults and the package's autotuner replaces them.  mlmc_get_tuning
+ * returns {variant, items_per_block, blocks_per_sm}.  The paper has no
+ * counterpart (launch configuration only; results change only by the FP64
+ * rounding of the regrouped sums). */
+int mlmc_set_tuning(int integrator, int precision, int variant, int items_per_block,
+                    int blocks_per_sm);
+int mlmc_get_tuning(int integrator, int precision, int32_t out[3]);
+
 /* Bytes of device workspace that every entry point below needs for a batch
  * of up to `max_requests` level requests (1 for single-level calls).  The
  * workspace must be 256-byte aligned.  Pure host computation. */
@@ -244,6 +259,44 @@ int mlmc_estimate_graph(double eps, int integrator, const mlmc_params* p, uint64
 int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator,
                        const mlmc_params* p, uint64_t seed, void* workspace,
                        size_t ws_bytes, void* stream, mlmc_result* out);
+
+/* ------------------------------------------------------------- serving */
+/* A continuous-batching server of dispersion queries (the operational use
+ * the paper's introduction motivates).  Each query is an adaptive MLMC
+ * estimate (the rule of mlmc_estimate) of its own scenario and tolerance;
+ * its Philox stream is p->stream_id, the key is the server's seed.
+ *   mlmc_server_workspace_bytes  device workspace for max_active queries
+ *                                (model slots, request table, partials)
+ *   mlmc_server_create   binds the workspace and stream; allocates only
+ *                        pinned host staging buffers
+ *   mlmc_server_submit   validates and queues a query; returns its id
+ *   mlmc_server_tick     admits queued queries while a slot is free, runs
+ *                        ONE persistent launch over the pending samples of
+ *                        every active query (as many whole queries as the
+ *                        tick's 2048 requests / 32768 work items allow),
+ *                        reduces each request in item order, advances each
+ *                        query's driver and retires finished queries;
+ *                        synchronises the stream.  n_done: queries finished
+ *                        in this tick; n_active: queries left (active and
+ *                        queued)
+ *   mlmc_server_poll     1 while the query runs; its final status (MLMC_OK,
+ *                        MLMC_ENOTCONV, MLMC_ENONFINITE) with the result and
+ *                        its submit-to-finish latency once done
+ *   mlmc_server_release  forgets a finished query
+ *   mlmc_server_stats    out = {ticks, finished, path-steps, busy seconds,
+ *                        active, queued}
+ * A request's split into work items depends only on that request, so a
+ * query's result is bitwise the same alone and in any mix. */
+typedef struct mlmc_server_s* mlmc_server;
+size_t mlmc_server_workspace_bytes(int max_active);
+int mlmc_server_create(int integrator, int precision, int max_active, uint64_t seed,
+                       void* workspace, size_t ws_bytes, void* stream, mlmc_server* out);
+int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t* query_id);
+int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active);
+int mlmc_server_poll(mlmc_server s, uint64_t query_id, mlmc_result* out, double* latency_s);
+int mlmc_server_release(mlmc_server s, uint64_t query_id);
+int mlmc_server_stats(mlmc_server s, double out[6]);
+int mlmc_server_destroy(mlmc_server s);
 
 /* ---------------------------------------------------------- path outputs */
 /* Final states of N pairs of `level` into d_states (N x 4 values of the path

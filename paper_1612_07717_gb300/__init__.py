@@ -101,6 +101,17 @@ def lib():
         L.mlmc_graph_destroy.argtypes = [vp]
         L.mlmc_estimate_graph.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
                                           vp, C.POINTER(Result)]
+        L.mlmc_set_tuning.argtypes = [i32, i32, i32, i32, i32]
+        L.mlmc_get_tuning.argtypes = [i32, i32, C.POINTER(C.c_int32)]
+        L.mlmc_server_workspace_bytes.restype = C.c_size_t
+        L.mlmc_server_workspace_bytes.argtypes = [i32]
+        L.mlmc_server_create.argtypes = [i32, i32, i32, u64, vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.mlmc_server_submit.argtypes = [vp, C.POINTER(Params), C.c_double, C.POINTER(u64)]
+        L.mlmc_server_tick.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.mlmc_server_poll.argtypes = [vp, u64, C.POINTER(Result), C.POINTER(C.c_double)]
+        L.mlmc_server_release.argtypes = [vp, u64]
+        L.mlmc_server_stats.argtypes = [vp, C.POINTER(C.c_double)]
+        L.mlmc_server_destroy.argtypes = [vp]
         L.mlmc_stmc_estimate.argtypes = [C.c_double, i32, i32, i32, C.POINTER(Params), u64, vp,
                                          C.c_size_t, vp, C.POINTER(Result)]
         L.mlmc_level_paths_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
@@ -336,3 +347,75 @@ def path_trace(level, N, integrator, params, seed, path_offset=0, stream=None):
                                      _stream_handle(stream))
     _check(rc, "mlmc_path_trace_async")
     return tf, tc
+
+
+class Server:
+    """Continuous-batching server of dispersion queries (``mlmc_server_*``).
+
+    ``submit`` queues a query (a ``Params`` with its own scenario and
+    ``stream_id``) with its tolerance; ``tick`` runs one batched launch over
+    every active query and retires the finished ones; ``poll`` returns a
+    finished query's result and latency.
+    """
+
+    def __init__(self, integrator=BAOAB, precision=FP32, max_active=64, seed=1, stream=None):
+        import torch
+        self.integrator, self.precision = integrator, precision
+        nbytes = int(lib().mlmc_server_workspace_bytes(max_active))
+        self._buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self._buf.data_ptr() + 255) // 256 * 256
+        self.stream = stream
+        self.handle = C.c_void_p()
+        rc = lib().mlmc_server_create(integrator, precision, max_active, seed, C.c_void_p(ptr),
+                                      nbytes, _stream_handle(stream), C.byref(self.handle))
+        _check(rc, "mlmc_server_create")
+
+    def submit(self, params, eps):
+        qid = C.c_uint64()
+        _check(lib().mlmc_server_submit(self.handle, C.byref(params), eps, C.byref(qid)),
+               "mlmc_server_submit")
+        return qid.value
+
+    def tick(self):
+        nd, na = C.c_int(), C.c_int()
+        _check(lib().mlmc_server_tick(self.handle, C.byref(nd), C.byref(na)), "mlmc_server_tick")
+        return nd.value, na.value
+
+    def poll(self, qid, level_min=0):
+        r = Result()
+        lat = C.c_double()
+        rc = lib().mlmc_server_poll(self.handle, qid, C.byref(r), C.byref(lat))
+        if rc == 1:
+            return None
+        _check(rc, "mlmc_server_poll", allow=(ENONFINITE, ENOTCONV))
+        out = _result(r, level_min)
+        out["status"] = rc
+        out["latency_s"] = lat.value
+        return out
+
+    def release(self, qid):
+        lib().mlmc_server_release(self.handle, qid)
+
+    def stats(self):
+        o = (C.c_double * 6)()
+        _check(lib().mlmc_server_stats(self.handle, o), "mlmc_server_stats")
+        return dict(ticks=int(o[0]), finished=int(o[1]), path_steps=o[2], busy_s=o[3],
+                    active=int(o[4]), queued=int(o[5]))
+
+    def run_until_idle(self, max_ticks=100000):
+        for _ in range(max_ticks):
+            _, left = self.tick()
+            if left == 0:
+                return
+        raise RuntimeError("server did not drain")
+
+    def close(self):
+        if self.handle:
+            lib().mlmc_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

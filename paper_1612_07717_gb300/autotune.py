@@ -1,0 +1,120 @@
+"""Autotuner of the persistent multi-level launch.
+
+For each (integrator, precision) it times the batched workload (all levels
+0..12 of the 600 m boundary layer, N_l = n0 * 10^(-l/2)) for every
+combination of
+
+* register-budget variant: the kernel compiled for 1 (uncapped), 3 or 4
+  resident 256-thread blocks per SM -- the block shape the SM runs;
+* items per resident block: how finely the planner splits each level into
+  work items, i.e. how many path pairs one thread integrates per item
+  (paths per thread = item paths / 256);
+
+keeps the fastest, and records it as JSON keyed by the GPU name.  ``apply``
+loads such a file into the library's tuning table (``mlmc_set_tuning``).
+"""
+import ctypes as C
+import json
+import os
+import time
+
+from . import BAOAB, FP32, FP64, GL, SE, MultilevelLaunch, lib, make_params
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_FILE = os.path.join(HERE, "tuning_gb300.json")
+VARIANTS = {FP32: (1, 3, 4), FP64: (1,)}
+ITEMS_PER_BLOCK = (4, 8, 16, 32, 64)
+
+
+def gpu_name():
+    import torch
+    return torch.cuda.get_device_name(0)
+
+
+def set_tuning(integrator, precision, variant, items_per_block, blocks_per_sm=0):
+    rc = lib().mlmc_set_tuning(integrator, precision, variant, items_per_block, blocks_per_sm)
+    if rc != 0:
+        raise ValueError("mlmc_set_tuning rejected %r" % ((integrator, precision, variant,
+                                                            items_per_block, blocks_per_sm),))
+
+
+def get_tuning(integrator, precision):
+    out = (C.c_int32 * 3)()
+    lib().mlmc_get_tuning(integrator, precision, out)
+    return dict(variant=out[0], items_per_block=out[1], blocks_per_sm=out[2])
+
+
+def _time_launch(integrator, precision, n0, reps=3):
+    import torch
+    d = W.bl600(integrator)
+    lm = d["level_min"]
+    sched = [(l, max(1, int(round(n * n0 / 1e9)))) for l, n in W.schedule_c4(levels=13, n0=1e9)
+             if l >= lm]
+    p = make_params(d, precision=precision)
+    launch = MultilevelLaunch([(l, 0, n) for l, n in sched], integrator, p, seed=1)
+    steps = sum(n * ((8 << l) * 3 // 2 if l > lm else (8 << l)) for l, n in sched)
+    launch.run()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        launch.run()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return steps / (best / 1e3)
+
+
+def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=3e8, verbose=False):
+    """Sweep the launch knobs; returns {key: best config and rate} and applies the best."""
+    out = {}
+    for prec in precisions:
+        for integ in integrators:
+            scale = n0 if prec == FP32 else n0 / 100.0
+            results = []
+            for var in VARIANTS[prec]:
+                for ipb in ITEMS_PER_BLOCK:
+                    set_tuning(integ, prec, var, ipb, 0)
+                    rate = _time_launch(integ, prec, scale)
+                    results.append((rate, var, ipb))
+                    if verbose:
+                        print("integ %d prec %d variant %d items/block %d: %.3e path-steps/s"
+                              % (integ, prec, var, ipb, rate), flush=True)
+            rate, var, ipb = max(results)
+            set_tuning(integ, prec, var, ipb, 0)
+            out["%d/%d" % (integ, prec)] = dict(variant=var, items_per_block=ipb, blocks_per_sm=0,
+                                                path_steps_per_s=rate,
+                                                sweep=[dict(variant=v, items_per_block=i,
+                                                            path_steps_per_s=r)
+                                                       for r, v, i in results])
+    return out
+
+
+def save(table, path=DEFAULT_FILE):
+    doc = dict(gpu=gpu_name(), when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+               workload="levels 0..12, N_l = n0 10^(-l/2), BL600 scenario", table=table)
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return path
+
+
+def apply(path=DEFAULT_FILE, require_gpu_match=True):
+    """Load a tuning file into the library; returns the table or None."""
+    if not os.path.exists(path):
+        return None
+    doc = json.load(open(path))
+    if require_gpu_match and doc.get("gpu") != gpu_name():
+        return None
+    for key, cfg in doc["table"].items():
+        integ, prec = (int(x) for x in key.split("/"))
+        set_tuning(integ, prec, cfg["variant"], cfg["items_per_block"], cfg.get("blocks_per_sm", 0))
+    return doc["table"]
+
+
+if __name__ == "__main__":
+    import sys
+    t = tune(precisions=(FP32, FP64), verbose=True)
+    print(save(t, sys.argv[1] if len(sys.argv) > 1 else DEFAULT_FILE))

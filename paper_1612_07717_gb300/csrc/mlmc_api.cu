@@ -10,36 +10,67 @@
 
 namespace mlmc {
 
-namespace prec_f32 {
-cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,
-                             unsigned int*, int, cudaStream_t);
-size_t model_size();
-void model_image(const HostModel&, void*);
-cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
-                           cudaStream_t);
-cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
-                       cudaStream_t);
-cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
-                       unsigned int*, int, cudaStream_t);
-cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*, int32_t*,
-                  void*, void*, bool, cudaStream_t);
-int occupancy(int, bool);
-}  // namespace prec_f32
-namespace prec_f64 {
-cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,
-                             unsigned int*, int, cudaStream_t);
-size_t model_size();
-void model_image(const HostModel&, void*);
-cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*, int,
-                           cudaStream_t);
-cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, Partial*, int,
-                       cudaStream_t);
-cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,
-                       unsigned int*, int, cudaStream_t);
-cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*, int32_t*,
-                  void*, void*, bool, cudaStream_t);
-int occupancy(int, bool);
-}  // namespace prec_f64
+// Launchers exported by the kernel translation units: prec_f32 / prec_f64
+// hold every kernel; prec_f32_b3 / prec_f32_b4 hold the persistent kernels
+// compiled for 3 and 4 resident blocks per SM (tighter register budgets).
+#define MLMC_DECLARE_MULTI(NS)                                                                 \
+  namespace NS {                                                                               \
+  cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,      \
+                         unsigned int*, int, cudaStream_t);                                     \
+  cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*,  \
+                             int, cudaStream_t);                                                \
+  cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,     \
+                               unsigned int*, int, cudaStream_t);                               \
+  int occupancy_multi(int);                                                                    \
+  }
+#define MLMC_DECLARE_ALL(NS)                                                                   \
+  MLMC_DECLARE_MULTI(NS)                                                                       \
+  namespace NS {                                                                               \
+  cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t,         \
+                         Partial*, int, cudaStream_t);                                          \
+  size_t model_size();                                                                         \
+  void model_image(const HostModel&, void*);                                                   \
+  cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*,       \
+                    int32_t*, void*, void*, bool, cudaStream_t);                                \
+  int occupancy(int, bool);                                                                    \
+  }
+MLMC_DECLARE_ALL(prec_f32)
+MLMC_DECLARE_ALL(prec_f64)
+MLMC_DECLARE_MULTI(prec_f32_b3)
+MLMC_DECLARE_MULTI(prec_f32_b4)
+
+// ---------------------------------------------------------------------------
+// Tuning table of the persistent kernels per (integrator, precision):
+// register-budget variant (resident blocks per SM the kernel is compiled
+// for: 1 = uncapped, 3, 4; FP64 has only 1), work items per resident block
+// in the planner, and resident blocks per SM actually launched (0 = as many
+// as fit).  The defaults are the best of a GB300 sweep; the autotuner
+// (paper_1612_07717_gb300/autotune.py) replaces them.
+// ---------------------------------------------------------------------------
+struct Tune {
+  int variant, items_per_block, blocks_per_sm;
+};
+static Tune g_tune[3][2] = {{{3, 16, 0}, {1, 16, 0}},   // SE
+                            {{3, 16, 0}, {1, 16, 0}},   // GL
+                            {{4, 16, 0}, {1, 16, 0}}};  // BAOAB
+static std::mutex g_tune_mu;
+
+static Tune tune_of(int prec, int integ) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune[integ][prec];
+}
+
+int items_per_block(int prec, int integ) { return tune_of(prec, integ).items_per_block; }
+
+#define MLMC_DISPATCH_MULTI(prec, integ, CALL)                     \
+  do {                                                             \
+    if (prec) return prec_f64::CALL;                               \
+    switch (tune_of(prec, integ).variant) {                        \
+      case 3: return prec_f32_b3::CALL;                            \
+      case 4: return prec_f32_b4::CALL;                            \
+      default: return prec_f32::CALL;                              \
+    }                                                              \
+  } while (0)
 
 cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                               uint64_t N, uint64_t offset, Partial* partials, int grid,
@@ -50,22 +81,22 @@ cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const Le
 cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                               int n_req, uint32_t n_items, Partial* partials,
                               unsigned int* counter, int grid, cudaStream_t st) {
-  return prec ? prec_f64::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st)
-              : prec_f32::multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
+  MLMC_DISPATCH_MULTI(prec, integ,
+                      multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st));
 }
 cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, const DevPlan* plan,
                                   Partial* partials, unsigned int* counter, int grid,
                                   cudaStream_t st) {
-  return prec ? prec_f64::multilevel_dev(integ, hm, plan, partials, counter, grid, st)
-              : prec_f32::multilevel_dev(integ, hm, plan, partials, counter, grid, st);
+  MLMC_DISPATCH_MULTI(prec, integ, multilevel_dev(integ, hm, plan, partials, counter, grid, st));
 }
 cudaError_t launch_multilevel_table(int prec, int integ, const void* models, const PlanReq* reqs,
                                    int n_req, uint32_t n_items, Partial* partials,
                                    unsigned int* counter, int grid, cudaStream_t st) {
-  return prec ? prec_f64::multilevel_table(integ, models, reqs, n_req, n_items, partials, counter,
-                                           grid, st)
-              : prec_f32::multilevel_table(integ, models, reqs, n_req, n_items, partials, counter,
-                                           grid, st);
+  MLMC_DISPATCH_MULTI(prec, integ, multilevel_table(integ, models, reqs, n_req, n_items, partials,
+                                                    counter, grid, st));
+}
+static int occupancy_multi(int prec, int integ) {
+  MLMC_DISPATCH_MULTI(prec, integ, occupancy_multi(integ));
 }
 size_t model_bytes(int prec) { return prec ? prec_f64::model_size() : prec_f32::model_size(); }
 void model_image(int prec, const HostModel& hm, void* out) {
@@ -83,7 +114,11 @@ cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSp
               : prec_f32::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st);
 }
 int blocks_per_sm(int prec, int integ, bool multilevel) {
-  return prec ? prec_f64::occupancy(integ, multilevel) : prec_f32::occupancy(integ, multilevel);
+  if (!multilevel) return prec ? prec_f64::occupancy(integ, false) : prec_f32::occupancy(integ, false);
+  int nb = occupancy_multi(prec, integ);
+  const int want = tune_of(prec, integ).blocks_per_sm;
+  if (want > 0 && want < nb) nb = want;
+  return nb;
 }
 
 // ---------------------------------------------------------------------------
@@ -416,6 +451,29 @@ int mlmc_params_default(mlmc_params* p) {
   return MLMC_OK;
 }
 
+int mlmc_set_tuning(int integrator, int precision, int variant, int items_per_block,
+                    int blocks_per_sm) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (precision != MLMC_FP32 && precision != MLMC_FP64) return MLMC_EINVAL;
+  if (variant != 1 && variant != 3 && variant != 4) return MLMC_EINVAL;
+  if (precision == MLMC_FP64 && variant != 1) return MLMC_EINVAL;
+  if (items_per_block < 1 || items_per_block > 1024) return MLMC_EINVAL;
+  if (blocks_per_sm < 0 || blocks_per_sm > kMaxBlocksPerSM) return MLMC_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[integrator][precision] = Tune{variant, items_per_block, blocks_per_sm};
+  return MLMC_OK;
+}
+
+int mlmc_get_tuning(int integrator, int precision, int32_t out[3]) {
+  if (!out || integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (precision != MLMC_FP32 && precision != MLMC_FP64) return MLMC_EINVAL;
+  const Tune t = tune_of(precision, integrator);
+  out[0] = t.variant;
+  out[1] = t.items_per_block;
+  out[2] = t.blocks_per_sm;
+  return MLMC_OK;
+}
+
 int mlmc_device_info(int32_t out[3]) {
   if (!out) return MLMC_EINVAL;
   DevInfo di;
@@ -482,8 +540,8 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
     while (j >= 0 && reqs[order[j]].level < reqs[v].level) { order[j + 1] = order[j]; --j; }
     order[j + 1] = v;
   }
-  // about 16 items per resident block, bounded by kMaxItems
-  double target = total / (16.0 * (double)grid);
+  // about items_per_block items per resident block, bounded by kMaxItems
+  double target = total / ((double)items_per_block(p->precision, integ) * (double)grid);
   if (target < 1.0) target = 1.0;
   uint64_t items = 0;
   for (int pass = 0; pass < 40; ++pass) {

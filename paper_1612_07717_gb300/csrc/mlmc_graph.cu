@@ -20,7 +20,7 @@ constexpr int kMaxIterations = 4 * kLevels;  // a driver pass count that cannot 
 // Driver state in the workspace's graph region.
 struct GState {
   int32_t L, pass, iter, converged, status, lmin, Lmax, n_init;
-  int32_t M0, grid, done, pad;
+  int32_t M0, grid, done, items_per_block;
   double eps, T;
   uint64_t Ndone[kLevels], dN[kLevels];
   uint64_t n[kLevels], bad[kLevels], steps[kLevels];
@@ -40,12 +40,13 @@ __device__ __forceinline__ uint64_t dev_steps(const GState* g, int l) {
 }
 
 // Plan the levels with dN > 0, finest first, exactly as the host planner
-// does: items of about total / (16 * grid) path-steps, at least one block.
+// does: items of about total / (items_per_block * grid) path-steps, at
+// least one block.
 __device__ void plan_device(const GState* g, DevPlan* plan) {
   double total = 0.0;
   for (int l = g->L; l >= g->lmin; --l)
     if (g->dN[l]) total += (double)g->dN[l] * (double)dev_steps(g, l);
-  double target = total / (16.0 * (double)g->grid);
+  double target = total / ((double)g->items_per_block * (double)g->grid);
   if (target < 1.0) target = 1.0;
   for (int pass = 0; pass < 40; ++pass) {
     uint64_t items = 0;
@@ -106,7 +107,7 @@ __device__ void write_result(const GState* g, mlmc_result* out) {
 }
 
 __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, int Lmax, int n_init,
-                             int M0, int grid, double eps, double T) {
+                             int M0, int grid, int ipb, double eps, double T) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   GState* g = &r->g;
   memset(g, 0, sizeof(*g));
@@ -115,6 +116,7 @@ __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, in
   g->n_init = n_init;
   g->M0 = M0;
   g->grid = grid;
+  g->items_per_block = ipb;
   g->eps = eps;
   g->T = T;
   g->L = lmin;
@@ -259,7 +261,7 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
   CK(cudaStreamBeginCaptureToGraph(g->cap, g->graph, nullptr, nullptr, 0,
                                    cudaStreamCaptureModeThreadLocal));
   k_graph_init<<<1, 32, 0, g->cap>>>(g->region, w.counter, p->level_min, p->L_max, p->n_init,
-                                     p->M0, grid, eps, p->T);
+                                     p->M0, grid, items_per_block(prec, integrator), eps, p->T);
   CK(cudaGetLastError());
   CK(cudaStreamEndCapture(g->cap, &g->graph));
   CK(cudaGraphGetNodes(g->graph, &init_node, &n_nodes));

@@ -85,8 +85,10 @@ cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSp
                          cudaStream_t st);
 cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                          uint64_t N, uint64_t offset, void* d_tf, void* d_tc, cudaStream_t st);
-// Resident blocks per SM of the sums / multi-level kernels (occupancy query).
+// Resident blocks per SM of the sums / multi-level kernels (occupancy query
+// and tuning table), and the planner's work items per resident block.
 int blocks_per_sm(int prec, int integ, bool multilevel);
+int items_per_block(int prec, int integ);
 
 // Device facts, workspace carving and parameter handling (mlmc_api.cu).
 struct DevInfo {

@@ -15,12 +15,18 @@
 #include "mlmc_internal.h"
 
 // Minimum resident blocks per SM requested from the register allocator for
-// the path kernels (1: no register cap).
+// the path kernels (1: no register cap).  Each translation unit that
+// includes this file instantiates the kernels in its own namespace
+// MLMC_KNS, so variants with different register budgets can coexist.
 #ifndef MLMC_MINB
 #define MLMC_MINB 1
 #endif
+#ifndef MLMC_KNS
+#define MLMC_KNS kdefault
+#endif
 
 namespace mlmc {
+namespace MLMC_KNS {
 
 // ---------------------------------------------------------------------------
 // Host -> device constants
@@ -513,4 +519,5 @@ int blocks_per_sm_impl(int integ, bool multilevel) {
   return nb;
 }
 
+}  // namespace MLMC_KNS
 }  // namespace mlmc

@@ -1,37 +1,7 @@
-// mlmc_kernels_f64.cu -- double-precision instantiation of the path kernels.
-#include <cstring>
-
-#include "mlmc_kernels.cuh"
-
-namespace mlmc {
-namespace prec_f64 {
-cudaError_t level_sums(int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
-                       uint64_t offset, Partial* partials, int grid, cudaStream_t st) {
-  return level_sums_impl<double>(integ, hm, lv, N, offset, partials, grid, st);
-}
-cudaError_t multilevel(int integ, const HostModel& hm, const ReqPlan* plan, int n_req,
-                       uint32_t n_items, Partial* partials, unsigned int* counter, int grid,
-                       cudaStream_t st) {
-  return multilevel_impl<double>(integ, hm, plan, n_req, n_items, partials, counter, grid, st);
-}
-cudaError_t multilevel_dev(int integ, const HostModel& hm, const DevPlan* plan, Partial* partials,
-                           unsigned int* counter, int grid, cudaStream_t st) {
-  return multilevel_dev_impl<double>(integ, hm, plan, partials, counter, grid, st);
-}
-cudaError_t multilevel_table(int integ, const void* models, const PlanReq* reqs, int n_req,
-                             uint32_t n_items, Partial* partials, unsigned int* counter, int grid,
-                             cudaStream_t st) {
-  return multilevel_table_impl<double>(integ, models, reqs, n_req, n_items, partials, counter, grid, st);
-}
-size_t model_size() { return sizeof(Model<double>); }
-void model_image(const HostModel& hm, void* out) {
-  const Model<double> m = make_model<double>(hm);
-  memcpy(out, &m, sizeof(m));
-}
-cudaError_t paths(int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N, uint64_t offset,
-                  void* states, int32_t* flags, void* tf, void* tc, bool trace, cudaStream_t st) {
-  return paths_impl<double>(integ, hm, lv, N, offset, states, flags, tf, tc, trace, st);
-}
-int occupancy(int integ, bool multilevel) { return blocks_per_sm_impl<double>(integ, multilevel); }
-}  // namespace prec_f64
-}  // namespace mlmc
+// mlmc_kernels_f64.cu -- double precision, all kernels.
+#define MLMC_PREC double
+#define MLMC_NS prec_f64
+#define MLMC_KNS k_f64
+#define MLMC_MINB 1
+#define MLMC_ALL 1
+#include "mlmc_kernels_inst.inc"

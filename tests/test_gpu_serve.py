@@ -1,0 +1,50 @@
+"""The continuous-batching query server (GPU): results are bitwise the same
+alone and in a mix of other queries, agree with the stand-alone adaptive
+estimator, and every query finishes."""
+import pytest
+
+import paper_1612_07717_gb300 as G
+from paper_1612_07717_gb300 import serve as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _drain(srv, items):
+    ids = [srv.submit(G.make_params(d), eps) for _, d, eps in items]
+    srv.run_until_idle()
+    return [srv.poll(q) for q in ids]
+
+
+def test_results_are_identical_alone_and_in_the_mix():
+    qs = S.draw_queries(24, seed=11)
+    mix = _drain(G.Server(max_active=8), qs)           # 8 slots: queries wait, overlap, finish
+    for k in (0, 5, 17, 23):
+        alone = _drain(G.Server(max_active=8), [qs[k]])[0]
+        for key in ("estimate", "est_variance", "N", "V", "mean_y", "L", "converged",
+                    "total_path_steps"):
+            assert alone[key] == mix[k][key], (k, key)
+    assert all(r["status"] in (G.OK, G.ENOTCONV) for r in mix)
+
+
+def test_server_estimates_match_the_standalone_driver():
+    qs = S.draw_queries(6, seed=3)
+    got = _drain(G.Server(max_active=4), qs)
+    for (t, d, eps), r in zip(qs, got):
+        h = G.estimate(eps, G.BAOAB, G.make_params(d), 1)
+        assert h["L"] == r["L"]
+        for a, b in zip(h["N"], r["N"]):
+            assert abs(a - b) <= 1
+        assert r["estimate"][0] == pytest.approx(h["estimate"][0], rel=1e-9)
+
+
+def test_admission_respects_slots_and_everything_finishes():
+    srv = G.Server(max_active=3)
+    qs = S.draw_queries(10, seed=5)
+    ids = [srv.submit(G.make_params(d), eps) for _, d, eps in qs]
+    srv.tick()
+    st = srv.stats()
+    assert st["active"] + st["finished"] <= 3 + st["finished"] and st["queued"] >= 10 - 3 - st["finished"]
+    srv.run_until_idle()
+    assert srv.stats()["finished"] == 10
+    for q in ids:
+        assert srv.poll(q) is not None
