@@ -19,8 +19,8 @@ namespace mlmc {
                          unsigned int*, int, cudaStream_t);                                     \
   cudaError_t multilevel_dev(int, const HostModel&, const DevPlan*, Partial*, unsigned int*,  \
                              int, cudaStream_t);                                                \
-  cudaError_t multilevel_table(int, const void*, const PlanReq*, int, uint32_t, Partial*,     \
-                               unsigned int*, int, cudaStream_t);                               \
+  cudaError_t multilevel_table(int, const void*, size_t, const PlanReq*, int, uint32_t,       \
+                               Partial*, unsigned int*, int, cudaStream_t);                     \
   int occupancy_multi(int);                                                                    \
   }
 #define MLMC_DECLARE_ALL(NS)                                                                   \
@@ -89,11 +89,12 @@ cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, cons
                                   cudaStream_t st) {
   MLMC_DISPATCH_MULTI(prec, integ, multilevel_dev(integ, hm, plan, partials, counter, grid, st));
 }
-cudaError_t launch_multilevel_table(int prec, int integ, const void* models, const PlanReq* reqs,
-                                   int n_req, uint32_t n_items, Partial* partials,
-                                   unsigned int* counter, int grid, cudaStream_t st) {
-  MLMC_DISPATCH_MULTI(prec, integ, multilevel_table(integ, models, reqs, n_req, n_items, partials,
-                                                    counter, grid, st));
+cudaError_t launch_multilevel_table(int prec, int integ, const void* models, size_t stride,
+                                   const PlanReq* reqs, int n_req, uint32_t n_items,
+                                   Partial* partials, unsigned int* counter, int grid,
+                                   cudaStream_t st) {
+  MLMC_DISPATCH_MULTI(prec, integ, multilevel_table(integ, models, stride, reqs, n_req, n_items,
+                                                    partials, counter, grid, st));
 }
 static int occupancy_multi(int prec, int integ) {
   MLMC_DISPATCH_MULTI(prec, integ, occupancy_multi(integ));

@@ -73,10 +73,12 @@ cudaError_t launch_multilevel_dev(int prec, int integ, const HostModel& hm, cons
                                   Partial* partials, unsigned int* counter, int grid,
                                   cudaStream_t st);
 // Multi-query batches (serving): a table of requests in device memory, each
-// tagged with the slot of its query's Model in a device array of Models.
-cudaError_t launch_multilevel_table(int prec, int integ, const void* models, const PlanReq* reqs,
-                                   int n_req, uint32_t n_items, Partial* partials,
-                                   unsigned int* counter, int grid, cudaStream_t st);
+// tagged with the slot of its query's Model; slot k's Model starts at byte
+// k * stride of `models`.
+cudaError_t launch_multilevel_table(int prec, int integ, const void* models, size_t stride,
+                                   const PlanReq* reqs, int n_req, uint32_t n_items,
+                                   Partial* partials, unsigned int* counter, int grid,
+                                   cudaStream_t st);
 // Bytes of one device Model of precision prec, and its host image.
 size_t model_bytes(int prec);
 void model_image(int prec, const HostModel& hm, void* out);

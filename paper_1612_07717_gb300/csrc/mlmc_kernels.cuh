@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
 // query's sums are the same alone and in any mix.
 template <int INTEG, typename R>
 __global__ void __launch_bounds__(kBlock, MLMC_MINB)
-    k_multilevel_table(const Model<R>* __restrict__ models, const PlanReq* __restrict__ reqs,
-                       int n_req, uint32_t n_items, Partial* __restrict__ partials,
-                       unsigned int* __restrict__ counter) {
+    k_multilevel_table(const char* __restrict__ models, size_t model_stride,
+                       const PlanReq* __restrict__ reqs, int n_req, uint32_t n_items,
+                       Partial* __restrict__ partials, unsigned int* __restrict__ counter) {
   __shared__ unsigned int s_item;
   __shared__ int s_req;
   for (;;) {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB)
     __syncthreads();
     if (it >= n_items) break;
     const PlanReq pr = reqs[r];
-    const Model<R> m = models[pr.slot];
+    const Model<R> m = *(const Model<R>*)(models + (size_t)pr.slot * model_stride);
     Level<R> lv;
     lv.h = (R)pr.h;
     lv.h2 = (R)(0.5 * pr.h);
@@ -469,16 +469,19 @@ cudaError_t multilevel_dev_impl(int integ, const HostModel& hm, const DevPlan* p
 }
 
 template <typename R>
-cudaError_t multilevel_table_impl(int integ, const void* models, const PlanReq* reqs, int n_req,
-                                  uint32_t n_items, Partial* partials, unsigned int* counter,
-                                  int grid, cudaStream_t st) {
-  const Model<R>* mm = (const Model<R>*)models;
+cudaError_t multilevel_table_impl(int integ, const void* models, size_t stride, const PlanReq* reqs,
+                                  int n_req, uint32_t n_items, Partial* partials,
+                                  unsigned int* counter, int grid, cudaStream_t st) {
+  const char* mm = (const char*)models;
   if (integ == kSE)
-    k_multilevel_table<kSE, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
+    k_multilevel_table<kSE, R><<<grid, kBlock, 0, st>>>(mm, stride, reqs, n_req, n_items, partials,
+                                                        counter);
   else if (integ == kGL)
-    k_multilevel_table<kGL, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
+    k_multilevel_table<kGL, R><<<grid, kBlock, 0, st>>>(mm, stride, reqs, n_req, n_items, partials,
+                                                        counter);
   else
-    k_multilevel_table<kBAOAB, R><<<grid, kBlock, 0, st>>>(mm, reqs, n_req, n_items, partials, counter);
+    k_multilevel_table<kBAOAB, R><<<grid, kBlock, 0, st>>>(mm, stride, reqs, n_req, n_items,
+                                                           partials, counter);
   return cudaGetLastError();
 }
 

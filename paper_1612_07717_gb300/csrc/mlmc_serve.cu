@@ -319,9 +319,9 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->d_reqs, s->h_reqs, n_req * sizeof(PlanReq),
                                               cudaMemcpyHostToDevice, st));
     if (!rc) rc = cuda_status(cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned int), st));
-    if (!rc) rc = cuda_status(launch_multilevel_table(s->prec, s->integ, s->d_models, s->d_reqs,
-                                                      n_req, (uint32_t)items, s->d_partials,
-                                                      s->d_counter, s->grid, st));
+    if (!rc) rc = cuda_status(launch_multilevel_table(s->prec, s->integ, s->d_models, kModelSlot,
+                                                      s->d_reqs, n_req, (uint32_t)items,
+                                                      s->d_partials, s->d_counter, s->grid, st));
     if (!rc) rc = cuda_status(launch_finalize_table(s->d_partials, s->d_reqs, n_req, s->d_results, st));
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->h_results, s->d_results,
                                               n_req * sizeof(mlmc_level_result),
