@@ -366,6 +366,66 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
 }
 
 /* ------------------------------------------------------------------------ */
+/* Smoothed indicator, Section 4.1 (Eqs. conc, gr, SmoothedIndicator).      */
+/* p_r(s) = sum_k c_k s^k, k = 0..r+1, solves                               */
+/*   p(-1) = 1,  p(1) = 0,                                                  */
+/*   int_{-1}^{1} s^j p(s) ds = (-1)^j / (j + 1),  j = 0..r-1,              */
+/* with int_{-1}^{1} s^m ds = 2 / (m + 1) for even m and 0 for odd m.        */
+/* Gaussian elimination with partial pivoting, FP64.                        */
+/* ------------------------------------------------------------------------ */
+int orc_smooth_poly(int r, double* coef) {
+  if (r < 0 || r > 20) return -1;
+  const int n = r + 2;
+  double A[22][23];
+  memset(A, 0, sizeof(A));
+  for (int k = 0; k < n; ++k) {
+    A[0][k] = (k % 2 == 0) ? 1.0 : -1.0;   /* p(-1) */
+    A[1][k] = 1.0;                          /* p(1)  */
+  }
+  A[0][n] = 1.0;
+  A[1][n] = 0.0;
+  for (int j = 0; j < r; ++j) {
+    for (int k = 0; k < n; ++k) {
+      int m = j + k;
+      A[2 + j][k] = (m % 2 == 0) ? 2.0 / (double)(m + 1) : 0.0;
+    }
+    A[2 + j][n] = ((j % 2 == 0) ? 1.0 : -1.0) / (double)(j + 1);
+  }
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(A[i][c]) > fabs(A[piv][c])) piv = i;
+    if (A[piv][c] == 0.0) return -1;
+    if (piv != c)
+      for (int k = 0; k <= n; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+    for (int i = c + 1; i < n; ++i) {
+      double f = A[i][c] / A[c][c];
+      for (int k = c; k <= n; ++k) A[i][k] -= f * A[c][k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double v = A[i][n];
+    for (int k = i + 1; k < n; ++k) v -= A[i][k] * coef[k];
+    coef[i] = v / A[i][i];
+  }
+  return 0;
+}
+
+double orc_g(int r, const double* coef, double x) {
+  if (x < -1.0) return 1.0;
+  if (x > 1.0) return 0.0;
+  double v = 0.0;
+  for (int k = r + 1; k >= 0; --k) v = v * x + coef[k];
+  return v;
+}
+
+/* P^{r,delta}_{[a,b]}(X) = g_r((X - b) / delta) - g_r((X - a) / delta). */
+static double smoothed_interval(const orc_params* p, const double* coef, double X) {
+  return orc_g(p->smooth_r, coef, (X - p->qoi_b) / p->smooth_delta) -
+         orc_g(p->smooth_r, coef, (X - p->qoi_a) / p->smooth_delta);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Level sums, Eq. (Yhatell): Y = P_l - P_{l-1} per pair (Y = P on the      */
 /* coarsest level), for the QoIs P = X_T and P = 1[X_T < threshold].  Sums  */
 /* use Neumaier's compensated summation in a fixed order: paths in chunks   */
@@ -388,6 +448,7 @@ typedef struct {
 
 typedef struct {
   const orc_params* p;
+  const double* coef;       /* smoothing polynomial when qoi1_mode == 1 */
   int integ, level;
   uint64_t offset, N, seed;
   uint64_t first_chunk, n_chunks;
@@ -407,9 +468,14 @@ static void run_chunk(const work_t* w, uint64_t chunk, chunk_t* out) {
     if (r.nonfinite) { out->bad++; continue; }
     double Pf[2], Pc[2];
     Pf[0] = r.zf;
-    Pf[1] = (r.zf < w->p->qoi_threshold) ? 1.0 : 0.0;
     Pc[0] = coupled ? r.zc : 0.0;
-    Pc[1] = coupled ? ((r.zc < w->p->qoi_threshold) ? 1.0 : 0.0) : 0.0;
+    if (w->p->qoi1_mode == 1) {
+      Pf[1] = smoothed_interval(w->p, w->coef, r.zf);
+      Pc[1] = coupled ? smoothed_interval(w->p, w->coef, r.zc) : 0.0;
+    } else {
+      Pf[1] = (r.zf < w->p->qoi_threshold) ? 1.0 : 0.0;
+      Pc[1] = coupled ? ((r.zc < w->p->qoi_threshold) ? 1.0 : 0.0) : 0.0;
+    }
     for (int q = 0; q < 2; ++q) {
       double Y = Pf[q] - Pc[q];
       csum_add(&out->sum[q][0], Y);
@@ -447,6 +513,9 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
   const int coupled = level > pp.level_min;
   if (threads < 1) threads = 1;
   if (threads > 256) threads = 256;
+  double coef[24];
+  if (pp.qoi1_mode == 1 && (orc_smooth_poly(pp.smooth_r, coef) != 0 || !(pp.smooth_delta > 0.0)))
+    return -1;
 
   csum_t tot[2][6];
   memset(tot, 0, sizeof(tot));
@@ -462,7 +531,7 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
     if (nb > BATCH) nb = BATCH;
     volatile uint64_t next = 0;
     work_t w;
-    w.p = &pp; w.integ = integ; w.level = level; w.offset = offset; w.N = N;
+    w.p = &pp; w.coef = coef; w.integ = integ; w.level = level; w.offset = offset; w.N = N;
     w.seed = seed; w.first_chunk = first; w.n_chunks = nb; w.chunks = chunks;
     w.next = &next; w.lock = &lock;
     int nt = threads;
@@ -592,5 +661,113 @@ int orc_estimate(const orc_params* pin, int integ, double eps, uint64_t seed,
     out->total_path_steps += S[l].path_steps;
     out->n_nonfinite += S[l].n_nonfinite;
   }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binned density, Section 5.3 (Eq. vector_QoI): bin i = [a_i, a_{i+1}),    */
+/* a_i = i H / k, QoI P_i = P^{r,delta}_{[a_i, a_{i+1}]}(X_T); per bin the   */
+/* six sums of Y_i = P_i(fine) - P_i(coarse).  Same fixed chunk order and    */
+/* Neumaier sums as orc_level_sums.                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_params* p;
+  const double* coef;
+  int integ, level, k;
+  uint64_t offset, N, seed, n_chunks;
+  csum_t* sums;        /* n_chunks x k x 6 */
+  uint64_t* n_ok;      /* n_chunks */
+  volatile uint64_t* next;
+  pthread_mutex_t* lock;
+} pdf_work_t;
+
+static void pdf_chunk(const pdf_work_t* w, uint64_t chunk) {
+  const orc_params* p = w->p;
+  const int coupled = w->level > p->level_min;
+  const int k = w->k;
+  csum_t* S = w->sums + chunk * (uint64_t)k * 6;
+  memset(S, 0, sizeof(csum_t) * (size_t)k * 6);
+  w->n_ok[chunk] = 0;
+  uint64_t a = chunk * CHUNK, b = a + CHUNK;
+  if (b > w->N) b = w->N;
+  for (uint64_t j = a; j < b; ++j) {
+    orc_path_out r;
+    orc_path(p, w->integ, w->level, w->offset + j, w->seed, &r, NULL, NULL);
+    if (r.nonfinite) continue;
+    for (int i = 0; i < k; ++i) {
+      double lo = p->H * (double)i / (double)k, hi = p->H * (double)(i + 1) / (double)k;
+      double Pf = orc_g(p->smooth_r, w->coef, (r.zf - hi) / p->smooth_delta) -
+                  orc_g(p->smooth_r, w->coef, (r.zf - lo) / p->smooth_delta);
+      double Pc = 0.0;
+      if (coupled)
+        Pc = orc_g(p->smooth_r, w->coef, (r.zc - hi) / p->smooth_delta) -
+             orc_g(p->smooth_r, w->coef, (r.zc - lo) / p->smooth_delta);
+      double Y = Pf - Pc;
+      csum_add(&S[6 * i + 0], Y);
+      csum_add(&S[6 * i + 1], Y * Y);
+      csum_add(&S[6 * i + 2], Pf);
+      csum_add(&S[6 * i + 3], Pf * Pf);
+      csum_add(&S[6 * i + 4], Pc);
+      csum_add(&S[6 * i + 5], Pc * Pc);
+    }
+    w->n_ok[chunk] += 1;
+  }
+}
+
+static void* pdf_worker(void* arg) {
+  pdf_work_t* w = (pdf_work_t*)arg;
+  for (;;) {
+    uint64_t c;
+    pthread_mutex_lock(w->lock);
+    c = *w->next;
+    *w->next = c + 1;
+    pthread_mutex_unlock(w->lock);
+    if (c >= w->n_chunks) break;
+    pdf_chunk(w, c);
+  }
+  return NULL;
+}
+
+int orc_level_pdf_sums(const orc_params* pin, int integ, int level, uint64_t N, uint64_t offset,
+                       uint64_t seed, int k, int threads, uint64_t* n_ok, double* out) {
+  orc_params pp = *pin;
+  if (orc_normalise(&pp) != 0) return -1;
+  if (integ < ORC_SE || integ > ORC_BAOAB || level < pp.level_min || k < 1 || k > 256) return -1;
+  if (!(pp.smooth_delta > 0.0)) return -1;
+  double coef[24];
+  if (orc_smooth_poly(pp.smooth_r, coef) != 0) return -1;
+  if (threads < 1) threads = 1;
+  if (threads > 256) threads = 256;
+  const uint64_t n_chunks = (N + CHUNK - 1) / CHUNK;
+  csum_t* sums = (csum_t*)malloc(sizeof(csum_t) * (size_t)(n_chunks ? n_chunks : 1) * k * 6);
+  uint64_t* nk = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n_chunks ? n_chunks : 1));
+  if (!sums || !nk) { free(sums); free(nk); return -1; }
+  pthread_mutex_t lock;
+  pthread_mutex_init(&lock, NULL);
+  volatile uint64_t next = 0;
+  pdf_work_t w;
+  w.p = &pp; w.coef = coef; w.integ = integ; w.level = level; w.k = k;
+  w.offset = offset; w.N = N; w.seed = seed; w.n_chunks = n_chunks;
+  w.sums = sums; w.n_ok = nk; w.next = &next; w.lock = &lock;
+  int nt = threads;
+  if ((uint64_t)nt > n_chunks) nt = (int)(n_chunks ? n_chunks : 1);
+  if (nt <= 1) {
+    pdf_worker(&w);
+  } else {
+    pthread_t tid[256];
+    for (int t = 0; t < nt; ++t) pthread_create(&tid[t], NULL, pdf_worker, &w);
+    for (int t = 0; t < nt; ++t) pthread_join(tid[t], NULL);
+  }
+  pthread_mutex_destroy(&lock);
+  uint64_t tot_n = 0;
+  for (int i = 0; i < k * 6; ++i) {
+    csum_t acc = {0.0, 0.0};
+    for (uint64_t c = 0; c < n_chunks; ++c) csum_add(&acc, csum_val(&sums[c * (uint64_t)k * 6 + i]));
+    out[i] = csum_val(&acc);
+  }
+  for (uint64_t c = 0; c < n_chunks; ++c) tot_n += nk[c];
+  *n_ok = tot_n;
+  free(sums);
+  free(nk);
   return 0;
 }

@@ -47,7 +47,12 @@ typedef struct {
   int32_t n_init;       /* initial samples on a new level (adaptive driver)         */
   int32_t uniform_map;  /* ORC_U23 or ORC_U32                                       */
   uint32_t stream_id;   /* Philox counter word 3 (one stream per query)             */
-  int32_t pad_;
+  int32_t qoi1_mode;    /* QoI 1: 0 indicator 1[z(T) < qoi_threshold];
+                           1 smoothed interval P^{r,delta}_{[qoi_a, qoi_b]}(z(T))     */
+  double qoi_a, qoi_b;  /* interval of the smoothed QoI [m]                          */
+  double smooth_delta;  /* smoothing width delta [m]                                 */
+  int32_t smooth_r;     /* smoothing order r (p_r has degree r + 1)                  */
+  int32_t pad2_;
 } orc_params;
 
 typedef struct {
@@ -103,6 +108,20 @@ int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t see
  * result does not depend on the thread count. */
 int orc_level_sums(const orc_params* p, int integ, int level, uint64_t N,
                    uint64_t offset, uint64_t seed, int threads, orc_level_sums_t* out);
+
+/* Smoothing polynomial p_r of Section 4.1: degree r + 1, p(-1) = 1,
+ * p(1) = 0, and its first r moments on [-1, 1] equal those of the step
+ * function.  coef[k] multiplies s^k, k = 0..r+1.  Returns 0 or -1. */
+int orc_smooth_poly(int r, double* coef);
+
+/* g_r(x): 1 for x < -1, p_r(x) on [-1, 1], 0 for x > 1 (Eq. gr). */
+double orc_g(int r, const double* coef, double x);
+
+/* Level sums of the binned density (Section 5.3, Eq. vector_QoI): k bins
+ * [i H / k, (i + 1) H / k), each QoI the smoothed interval P^{r,delta};
+ * out[6 * i + j] as the six sums of orc_level_sums for bin i. */
+int orc_level_pdf_sums(const orc_params* p, int integ, int level, uint64_t N, uint64_t offset,
+                       uint64_t seed, int k, int threads, uint64_t* n_ok, double* out);
 
 /* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Giles 2008, Section 5). */
 int orc_estimate(const orc_params* p, int integ, double eps, uint64_t seed,

@@ -25,7 +25,8 @@ class Params(C.Structure):
         ("w0_mode", C.c_int32), ("M0", C.c_int32), ("level_min", C.c_int32),
         ("L_max", C.c_int32), ("coupling", C.c_int32), ("drift_outside", C.c_int32),
         ("n_init", C.c_int32), ("uniform_map", C.c_int32), ("stream_id", C.c_uint32),
-        ("pad_", C.c_int32),
+        ("qoi1_mode", C.c_int32), ("qoi_a", C.c_double), ("qoi_b", C.c_double),
+        ("smooth_delta", C.c_double), ("smooth_r", C.c_int32), ("pad2_", C.c_int32),
     ]
 
 
@@ -68,6 +69,12 @@ def lib():
                                C.POINTER(PathOut), C.c_void_p, C.c_void_p]
         L.orc_level_sums.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_uint64,
                                      C.c_uint64, C.c_uint64, C.c_int, C.POINTER(LevelSums)]
+        L.orc_smooth_poly.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        L.orc_g.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_double]
+        L.orc_g.restype = C.c_double
+        L.orc_level_pdf_sums.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                         C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_uint64),
+                                         C.POINTER(C.c_double)]
         L.orc_estimate.argtypes = [C.POINTER(Params), C.c_int, C.c_double, C.c_uint64,
                                    C.c_int, C.POINTER(Result)]
         _lib = L
@@ -77,7 +84,8 @@ def lib():
 _DEFAULTS = dict(u_star=0.2, f_coriolis=1e-4, H=0.0, kappa_sigma=1.3, kappa_tau=0.5, c_f=0.0,
                  eps_reg_frac=1e-3, z0=0.0, w0=0.0, T=1.0, qoi_threshold=0.0, w0_mode=0, M0=8,
                  level_min=0, L_max=10, coupling=0, drift_outside=0, n_init=10000,
-                 uniform_map=U32, stream_id=0)
+                 uniform_map=U32, stream_id=0, qoi1_mode=0, qoi_a=0.0, qoi_b=0.0,
+                 smooth_delta=0.0, smooth_r=4)
 
 
 def make_params(d=None, **kw):
@@ -172,3 +180,28 @@ def estimate(p, integ, eps, seed=1, threads=None):
                 V=[r.V[l] for l in range(lm, L + 1)],
                 mean_y=[r.mean_y[l] for l in range(lm, L + 1)],
                 total_path_steps=r.total_path_steps, n_nonfinite=r.n_nonfinite)
+
+
+def smooth_poly(r):
+    """Coefficients c_0..c_{r+1} of the smoothing polynomial p_r."""
+    c = (C.c_double * (r + 2))()
+    if lib().orc_smooth_poly(r, c) != 0:
+        raise ValueError("orc_smooth_poly failed for r=%d" % r)
+    return np.array(c[:])
+
+
+def g(r, coef, x):
+    c = (C.c_double * (r + 2))(*coef)
+    return lib().orc_g(r, c, float(x))
+
+
+def level_pdf_sums(p, integ, level, N, k, offset=0, seed=1, threads=None):
+    if threads is None:
+        threads = os.cpu_count() or 1
+    out = (C.c_double * (6 * k))()
+    n = C.c_uint64()
+    rc = lib().orc_level_pdf_sums(C.byref(p), integ, level, N, offset, seed, k, threads,
+                                  C.byref(n), out)
+    if rc != 0:
+        raise ValueError("orc_level_pdf_sums rejected its arguments")
+    return dict(n=n.value, sum=np.array(out[:]).reshape(k, 6))

@@ -23,7 +23,9 @@ def test_results_are_identical_alone_and_in_the_mix():
         for key in ("estimate", "est_variance", "N", "V", "mean_y", "L", "converged",
                     "total_path_steps"):
             assert alone[key] == mix[k][key], (k, key)
-    assert all(r["status"] in (G.OK, G.ENOTCONV) for r in mix)
+    # very coarse levels (h up to 450 s) can diverge a few paths: counted and excluded
+    assert all(r["status"] in (G.OK, G.ENOTCONV, G.ENONFINITE) for r in mix)
+    assert all(r["n_nonfinite"] <= 1e-3 * r["total_path_steps"] for r in mix)
 
 
 def test_server_estimates_match_the_standalone_driver():
