@@ -25,11 +25,25 @@ INTEGRATOR = 2          # BAOAB
 LEVELS = 13
 N0 = 1e9
 # FP32 arithmetic per path-step of a coupled BAOAB level, counted from the
-# step formulas as the kernel evaluates them (FMA = 2, other arithmetic,
-# square root, reciprocal, exp, log, sin, cos = 1 each); the derivation is
-# in the design doc.  Per coupled pair of fine steps: 3 BAOAB steps of 71, the
-# coarse coupling 9, two Box-Muller normals 12 -> 234 / 3 path-steps.
-FLOPS_PER_PATH_STEP = 78.0
+# step formulas as the kernel evaluates them (FMA = 2; add, multiply,
+# reciprocal, reciprocal square root, exp2, log2, sin, cos = 1; compares,
+# selects, min/max = 0); the derivation is in the design doc.  Per coupled pair
+# of fine steps: 3 BAOAB steps of 53, the coarse coupling 9 and one
+# Box-Muller pair 13 -> 181 / 3 path-steps.
+FLOPS_PER_PATH_STEP = 181.0 / 3.0
+# DRAM bytes per launch of the path kernel from an ncu capture, valid only
+# for the kernel sources it was taken with (their SHA-1 over csrc/).
+TRAFFIC = {"csrc_sha1": None, "bytes_per_launch": None}
+
+
+def csrc_sha1():
+    import hashlib
+    d = os.path.join(ROOT, "paper_1612_07717_gb300", "csrc")
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
 ORACLE_SAMPLE_SCALE = 2e-3
 
 
@@ -311,7 +325,9 @@ def main():
                        "tuning": tuning,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (TRAFFIC["bytes_per_launch"]
+                                     if TRAFFIC["csrc_sha1"] == csrc_sha1() else None),
                          "peak_source": "measured FFMA probe" if peak_probe else
                          "derived SMs*128*2*clock at %.0f MHz" % sm_mhz,
                          "flops_per_path_step": FLOPS_PER_PATH_STEP},

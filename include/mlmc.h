@@ -93,6 +93,12 @@ typedef struct mlmc_params {
   int32_t precision;    /* mlmc_precision of the path arithmetic                 */
   uint32_t stream_id;   /* Philox counter word 3: one random stream per query    */
   int32_t allow_unstable; /* 1: run SE levels with h lambda_max >= 2 anyway      */
+  int32_t qoi1_mode;    /* QoI 1: 0 indicator 1[z(T) < qoi_threshold]; 1 smoothed
+                           interval P^{r,delta}_{[qoi_a, qoi_b]}(z(T)) of Section 4.1
+                           (Eq. SmoothedIndicator)                                */
+  int32_t smooth_r;     /* smoothing order r, 0..10 (p_r has degree r + 1)      */
+  double qoi_a, qoi_b;  /* interval of the smoothed QoI [m], qoi_a < qoi_b       */
+  double smooth_delta;  /* smoothing width delta [m], > 0 when smoothing is used */
 } mlmc_params;
 
 /* Fill *p with the 600 m neutral boundary-layer scenario: u* = 0.2, f = 1e-4,
@@ -102,7 +108,8 @@ typedef struct mlmc_params {
 int mlmc_params_default(mlmc_params* p);
 
 /* ---------------------------------------------------------------- results */
-/* Per-level sums (Eq. Yhatell): for QoI q (0: z(T), 1: 1[z(T) < threshold])
+/* Per-level sums (Eq. Yhatell): for QoI q (0: z(T); 1: 1[z(T) < threshold] or
+ * the smoothed interval P^{r,delta}_{[a,b]}(z(T)), per qoi1_mode)
  * sum[q] = { sum Y, sum Y^2, sum P_f, sum P_f^2, sum P_c, sum P_c^2 } with
  * Y = P_f - P_c (Y = P_f and P_c = 0 on level_min).  FP64, Kahan-compensated
  * within thread blocks and reduced across blocks in a fixed order. */
@@ -259,6 +266,27 @@ int mlmc_estimate_graph(double eps, int integrator, const mlmc_params* p, uint64
 int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator,
                        const mlmc_params* p, uint64_t seed, void* workspace,
                        size_t ws_bytes, void* stream, mlmc_result* out);
+
+/* ------------------------------------------------------- binned density */
+/* The concentration field of Section 5.3 (Eq. vector_QoI): k equal bins
+ * [i H / k, (i + 1) H / k), i < k <= 32, each QoI the smoothed interval
+ * P^{r,delta} of its bin (order p->smooth_r, width p->smooth_delta > 0).
+ * mlmc_level_pdf_sums: N pairs of `level` from path_offset; out[2i] = sum
+ *   Y_i, out[2i + 1] = sum Y_i^2 (host array of 2k doubles), *n_ok finite
+ *   pairs, *n_nonfinite diverged pairs; synchronises the stream.
+ * mlmc_estimate_pdf: adaptive MLMC estimate of the k bin probabilities to
+ *   RMSE eps per bin, N_l chosen with max_i Var[Y_{l,i}] (Section 5.3) and
+ *   the bias test applied to every bin; pdf[i] (host, k doubles) gets bin
+ *   i's estimate; *out as mlmc_estimate with estimate[0] = sum_i pdf[i],
+ *   est_variance[0] the largest per-bin estimator variance, V[l] the largest
+ *   per-bin variance of level l. */
+int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
+                        uint64_t seed, uint64_t path_offset, int k, void* workspace,
+                        size_t ws_bytes, void* stream, double* out, uint64_t* n_ok,
+                        uint64_t* n_nonfinite);
+int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t seed, int k,
+                      void* workspace, size_t ws_bytes, void* stream, double* pdf,
+                      mlmc_result* out);
 
 /* ------------------------------------------------------------- serving */
 /* A continuous-batching server of dispersion queries (the operational use

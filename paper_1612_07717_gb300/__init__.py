@@ -37,7 +37,8 @@ class Params(C.Structure):
         ("w0_mode", C.c_int32), ("M0", C.c_int32), ("level_min", C.c_int32),
         ("L_max", C.c_int32), ("coupling", C.c_int32), ("drift_outside", C.c_int32),
         ("n_init", C.c_int32), ("precision", C.c_int32), ("stream_id", C.c_uint32),
-        ("allow_unstable", C.c_int32),
+        ("allow_unstable", C.c_int32), ("qoi1_mode", C.c_int32), ("smooth_r", C.c_int32),
+        ("qoi_a", C.c_double), ("qoi_b", C.c_double), ("smooth_delta", C.c_double),
     ]
 
 
@@ -59,7 +60,7 @@ class LevelRequest(C.Structure):
                 ("count", C.c_uint64)]
 
 
-assert C.sizeof(Params) == 128 and C.sizeof(LevelResult) == 128
+assert C.sizeof(Params) == 160 and C.sizeof(LevelResult) == 128
 
 
 class MLMCError(RuntimeError):
@@ -101,6 +102,11 @@ def lib():
         L.mlmc_graph_destroy.argtypes = [vp]
         L.mlmc_estimate_graph.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
                                           vp, C.POINTER(Result)]
+        L.mlmc_level_pdf_sums.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, i32, vp,
+                                          C.c_size_t, vp, C.POINTER(C.c_double),
+                                          C.POINTER(u64), C.POINTER(u64)]
+        L.mlmc_estimate_pdf.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, vp,
+                                        C.c_size_t, vp, C.POINTER(C.c_double), C.POINTER(Result)]
         L.mlmc_set_tuning.argtypes = [i32, i32, i32, i32, i32]
         L.mlmc_get_tuning.argtypes = [i32, i32, C.POINTER(C.c_int32)]
         L.mlmc_server_workspace_bytes.restype = C.c_size_t
@@ -307,6 +313,34 @@ class GraphEstimator:
             self.close()
         except Exception:
             pass
+
+
+def level_pdf_sums(level, N, integrator, params, seed, k, path_offset=0, workspace=None,
+                   stream=None):
+    """Per-bin sums (sum Y_i, sum Y_i^2) of the binned density on one level."""
+    ws = workspace or Workspace(params)
+    out = (C.c_double * (2 * k))()
+    nok, nbad = C.c_uint64(), C.c_uint64()
+    rc = lib().mlmc_level_pdf_sums(level, N, integrator, C.byref(params), seed, path_offset, k,
+                                   *ws.args(), _stream_handle(stream), out, C.byref(nok),
+                                   C.byref(nbad))
+    _check(rc, "mlmc_level_pdf_sums", allow=(ENONFINITE,))
+    return dict(n=nok.value, n_nonfinite=nbad.value,
+                sum=[[out[2 * i], out[2 * i + 1]] for i in range(k)])
+
+
+def estimate_pdf(eps, integrator, params, seed, k, workspace=None, stream=None):
+    """Adaptive MLMC estimate of the k-bin density (``mlmc_estimate_pdf``)."""
+    ws = workspace or Workspace(params)
+    pdf = (C.c_double * k)()
+    r = Result()
+    rc = lib().mlmc_estimate_pdf(eps, integrator, C.byref(params), seed, k, *ws.args(),
+                                 _stream_handle(stream), pdf, C.byref(r))
+    _check(rc, "mlmc_estimate_pdf", allow=(ENONFINITE, ENOTCONV))
+    out = _result(r, params.level_min)
+    out["pdf"] = list(pdf[:k])
+    out["status"] = rc
+    return out
 
 
 def stmc_estimate(eps, level, integrator, params, seed, n_pilot=10000, workspace=None,

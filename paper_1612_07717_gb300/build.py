@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libmlmc.so")
-SOURCES = ["mlmc_api.cu", "mlmc_graph.cu", "mlmc_serve.cu", "mlmc_kernels_f32.cu",
+SOURCES = ["mlmc_api.cu", "mlmc_graph.cu", "mlmc_serve.cu", "mlmc_pdf.cu", "mlmc_kernels_f32.cu",
            "mlmc_kernels_f32_b3.cu", "mlmc_kernels_f32_b4.cu", "mlmc_kernels_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 path kernels flush subnormals (no value of the path is subnormal

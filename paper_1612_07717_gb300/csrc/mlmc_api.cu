@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
 
 #include "mlmc_internal.h"
 
@@ -33,6 +34,8 @@ namespace mlmc {
   cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*,       \
                     int32_t*, void*, void*, bool, cudaStream_t);                                \
   int occupancy(int, bool);                                                                    \
+  cudaError_t pdf(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, int, double*,  \
+                  int, cudaStream_t);                                                           \
   }
 MLMC_DECLARE_ALL(prec_f32)
 MLMC_DECLARE_ALL(prec_f64)
@@ -114,6 +117,11 @@ cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSp
   return prec ? prec_f64::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st)
               : prec_f32::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st);
 }
+cudaError_t launch_pdf(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
+                       uint64_t offset, int k, double* partials, int grid, cudaStream_t st) {
+  return prec ? prec_f64::pdf(integ, hm, lv, N, offset, k, partials, grid, st)
+              : prec_f32::pdf(integ, hm, lv, N, offset, k, partials, grid, st);
+}
 int blocks_per_sm(int prec, int integ, bool multilevel) {
   if (!multilevel) return prec ? prec_f64::occupancy(integ, false) : prec_f32::occupancy(integ, false);
   int nb = occupancy_multi(prec, integ);
@@ -136,45 +144,43 @@ __device__ __forceinline__ void kadd(double& s, double& c, double x) {
 
 __device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint32_t end,
                              uint64_t path_steps, mlmc_level_result* __restrict__ out) {
-  __shared__ double s_v[kBlock / 32][6];
-  __shared__ unsigned long long s_u[kBlock / 32][5];
-  double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
-  unsigned long long u[5] = {0, 0, 0, 0, 0};
+  __shared__ double s_v[kBlock / 32][12];
+  __shared__ unsigned long long s_u[kBlock / 32][2];
+  double s[12], c[12];
+  for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
+  unsigned long long u[2] = {0, 0};
   for (uint32_t j = begin + threadIdx.x; j < end; j += kBlock) {
-    for (int k = 0; k < 6; ++k) kadd(s[k], c[k], p[j].s[k]);
-    u[0] += p[j].n; u[1] += p[j].bad; u[2] += p[j].nf; u[3] += p[j].nc; u[4] += p[j].nd;
+    for (int k = 0; k < 6; ++k) kadd(s[k], c[k], p[j].s0[k]);
+    for (int k = 0; k < 6; ++k) kadd(s[6 + k], c[6 + k], p[j].s1[k]);
+    u[0] += p[j].n;
+    u[1] += p[j].bad;
   }
-  double v[6];
-  for (int k = 0; k < 6; ++k) v[k] = s[k] - c[k];
+  double v[12];
+  for (int k = 0; k < 12; ++k) v[k] = s[k] - c[k];
   for (int off = 16; off > 0; off >>= 1) {
-    for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-    for (int k = 0; k < 5; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+    for (int k = 0; k < 2; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    for (int k = 0; k < 6; ++k) s_v[warp][k] = v[k];
-    for (int k = 0; k < 5; ++k) s_u[warp][k] = u[k];
+    for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
+    for (int k = 0; k < 2; ++k) s_u[warp][k] = u[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t[6] = {0, 0, 0, 0, 0, 0}, tc[6] = {0, 0, 0, 0, 0, 0};
-    unsigned long long q[5] = {0, 0, 0, 0, 0};
+    double t[12], tc[12];
+    for (int k = 0; k < 12; ++k) t[k] = tc[k] = 0.0;
+    unsigned long long q[2] = {0, 0};
     for (int w = 0; w < kBlock / 32; ++w) {
-      for (int k = 0; k < 6; ++k) kadd(t[k], tc[k], s_v[w][k]);
-      for (int k = 0; k < 5; ++k) q[k] += s_u[w][k];
+      for (int k = 0; k < 12; ++k) kadd(t[k], tc[k], s_v[w][k]);
+      for (int k = 0; k < 2; ++k) q[k] += s_u[w][k];
     }
     out->n = q[0];
     out->n_nonfinite = q[1];
     out->path_steps = path_steps;
     out->reserved = 0;
     for (int k = 0; k < 6; ++k) out->sum[0][k] = t[k] - tc[k];
-    const double nf = (double)q[2], nc = (double)q[3], nd = (double)q[4];
-    out->sum[1][0] = nf - nc;
-    out->sum[1][1] = nd;
-    out->sum[1][2] = nf;
-    out->sum[1][3] = nf;
-    out->sum[1][4] = nc;
-    out->sum[1][5] = nc;
+    for (int k = 0; k < 6; ++k) out->sum[1][k] = t[6 + k] - tc[6 + k];
   }
 }
 
@@ -268,6 +274,21 @@ int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
   if (p->coupling < 0 || p->coupling > 1) return MLMC_EINVAL;
   if (p->drift_outside < 0 || p->drift_outside > 1) return MLMC_EINVAL;
   if (p->precision != MLMC_FP32 && p->precision != MLMC_FP64) return MLMC_EINVAL;
+  if (p->qoi1_mode < 0 || p->qoi1_mode > 1) return MLMC_EINVAL;
+  hm->qoi1_mode = p->qoi1_mode;
+  hm->smooth_r = p->smooth_r;
+  hm->qa = p->qoi_a;
+  hm->qb = p->qoi_b;
+  hm->delta = p->smooth_delta;
+  for (int k = 0; k < kMaxSmoothR + 2; ++k) hm->pc[k] = 0.0;
+  if (p->qoi1_mode == 1 || p->smooth_delta > 0.0) {
+    if (p->smooth_r < 0 || p->smooth_r > kMaxSmoothR) return MLMC_EINVAL;
+    if (!(p->smooth_delta > 0.0) || !std::isfinite(p->smooth_delta)) return MLMC_EINVAL;
+    if (p->qoi1_mode == 1 &&
+        (!(p->qoi_a < p->qoi_b) || !std::isfinite(p->qoi_a) || !std::isfinite(p->qoi_b)))
+      return MLMC_EINVAL;
+    if (smooth_coefficients(p->smooth_r, hm->pc) != 0) return MLMC_EINVAL;
+  }
   const double A = p->kappa_sigma * us;
   hm->H = H;
   hm->eps = p->eps_reg_frac * H;
@@ -307,6 +328,44 @@ int level_spec(const HostModel& hm, int level, LevelSpec* ls) {
   ls->coupled = level > hm.level_min;
   if (ls->coupled && (M & 1)) return MLMC_EINVAL;
   return MLMC_OK;
+}
+
+// Smoothing polynomial of Section 4.1: p_r has degree r + 1, p(-1) = 1,
+// p(1) = 0 and the first r moments of the step function on [-1, 1].  The
+// conditions are invariant under s -> -s, p -> 1 - p, so the unique solution
+// is p(s) = 1/2 - q(s) with q odd: q(s) = sum_{k odd <= r+1} b_k s^k,
+//   q(1) = 1/2,   int_{-1}^{1} s^j q(s) ds = 1 / (j + 1) for odd j < r
+// (even moments hold by symmetry).  Solved by Gaussian elimination.
+int smooth_coefficients(int r, double* c) {
+  if (r < 0 || r > kMaxSmoothR) return -1;
+  int ks[kMaxSmoothR + 2], n = 0;
+  for (int k = 1; k <= r + 1; k += 2) ks[n++] = k;
+  double A[kMaxSmoothR][kMaxSmoothR + 1];
+  int row = 0;
+  for (int i = 0; i < n; ++i) A[row][i] = 1.0;           // q(1) = 1/2
+  A[row][n] = 0.5;
+  ++row;
+  for (int j = 1; j < r && row < n; j += 2, ++row) {     // odd moments
+    for (int i = 0; i < n; ++i) A[row][i] = 2.0 / (double)(j + ks[i] + 1);
+    A[row][n] = 1.0 / (double)(j + 1);
+  }
+  if (row != n) return -1;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < n; ++i)
+      if (std::fabs(A[i][col]) > std::fabs(A[piv][col])) piv = i;
+    if (A[piv][col] == 0.0) return -1;
+    for (int k = 0; k <= n; ++k) std::swap(A[col][k], A[piv][k]);
+    for (int i = 0; i < n; ++i) {
+      if (i == col) continue;
+      const double f = A[i][col] / A[col][col];
+      for (int k = col; k <= n; ++k) A[i][k] -= f * A[col][k];
+    }
+  }
+  for (int k = 0; k < kMaxSmoothR + 2; ++k) c[k] = 0.0;
+  c[0] = 0.5;
+  for (int i = 0; i < n; ++i) c[ks[i]] = -A[i][n] / A[i][i];
+  return 0;
 }
 
 // lambda is largest at the regularisation height (it falls with z).
@@ -449,6 +508,11 @@ int mlmc_params_default(mlmc_params* p) {
   p->precision = MLMC_FP32;
   p->stream_id = 0;
   p->allow_unstable = 0;
+  p->qoi1_mode = 0;
+  p->smooth_r = 4;
+  p->qoi_a = 0.0;
+  p->qoi_b = 0.0;
+  p->smooth_delta = 0.0;
   return MLMC_OK;
 }
 

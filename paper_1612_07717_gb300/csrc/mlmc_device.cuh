@@ -35,6 +35,10 @@ struct Model {
   R lim;                // 1e3 H: a path beyond it has diverged
   int32_t w0_mode, coupling;
   uint32_t stream_id;
+  int32_t qoi1_mode;    // 0 indicator, 1 smoothed interval
+  int32_t sdeg;         // degree of the smoothing polynomial (r + 1)
+  R qa, qb, idelta;     // interval and 1 / delta of the smoothed QoI
+  R pc[12];             // smoothing polynomial coefficients
   uint32_t rk0[10], rk1[10];  // Philox round keys of the seed
 };
 
@@ -212,6 +216,22 @@ __device__ __forceinline__ void drift_coef(const Model<R>& m, R z, R& g0, R& g1)
   const R t = rsqrt_(s);
   g0 = (inb ? m.hD : m.hD_out) * (s * t);
   g1 = (inb ? m.hDs : m.hDs_out) * (t * t);
+}
+
+// ---------------------------------------------------------------------------
+// Smoothed indicator (Section 4.1, Eqs. gr and SmoothedIndicator):
+// g_r(x) = 1 for x < -1, p_r(x) on [-1, 1], 0 for x > 1, and
+// P^{r,delta}_{[a,b]}(z) = g_r((z - b) / delta) - g_r((z - a) / delta).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R g_smooth(const Model<R>& m, R x) {
+  R v = m.pc[11];
+  for (int k = 10; k >= 0; --k) v = fma(v, x, m.pc[k]);
+  return x < R(-1) ? R(1) : (x > R(1) ? R(0) : v);
+}
+template <typename R>
+__device__ __forceinline__ R smoothed_interval(const Model<R>& m, R z) {
+  return g_smooth(m, (z - m.qb) * m.idelta) - g_smooth(m, (z - m.qa) * m.idelta);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,22 +13,29 @@ constexpr int kMaxReq = 32;          // requests in one multi-level launch
 constexpr int kMaxItems = 32768;     // work items in one multi-level launch
 constexpr int kMaxBlocksPerSM = 8;   // 2048 threads / kBlock
 
-// Partial sums of one thread block (or one work item), 128 bytes.
+// Partial sums of one thread block (or one work item), 128 bytes: for each
+// QoI sum Y, Y^2, P_f, P_f^2, P_c, P_c^2 (the indicator's sums are integer
+// counts held exactly in doubles), the finite pairs and the diverged pairs.
 struct Partial {
-  double s[6];  // QoI 0: sum Y, Y^2, P_f, P_f^2, P_c, P_c^2 (compensated)
-  unsigned long long n, bad, nf, nc, nd;  // QoI 1 counts: P_f = 1, P_c = 1, P_f != P_c
-  unsigned long long pad[5];
+  double s0[6], s1[6];
+  unsigned long long n, bad, pad[2];
 };
 static_assert(sizeof(Partial) == 128, "Partial layout");
 static_assert(sizeof(mlmc_level_result) == 128, "mlmc_level_result layout");
 
 // Scenario in double precision, derived once from mlmc_params.
+constexpr int kMaxSmoothR = 10;
 struct HostModel {
   double H, eps, A, inv_ktau, cfu, hD, hDs, qthr, z0, w0, T;
   int32_t w0_mode, coupling, drift_outside, M0, level_min;
   uint32_t stream_id;
   uint32_t rk0[10], rk1[10];
+  int32_t qoi1_mode, smooth_r;        // smoothed interval QoI (Section 4.1)
+  double qa, qb, delta;
+  double pc[kMaxSmoothR + 2];         // p_r(s) = sum_k pc[k] s^k
 };
+// Coefficients of the smoothing polynomial p_r (Section 4.1); 0 or -1.
+int smooth_coefficients(int r, double* c);
 
 struct LevelSpec {
   int level;
@@ -79,6 +86,9 @@ cudaError_t launch_multilevel_table(int prec, int integ, const void* models, siz
                                    const PlanReq* reqs, int n_req, uint32_t n_items,
                                    Partial* partials, unsigned int* counter, int grid,
                                    cudaStream_t st);
+// Binned density of one level (k bins): per block 2k + 2 doubles.
+cudaError_t launch_pdf(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
+                       uint64_t offset, int k, double* partials, int grid, cudaStream_t st);
 // Bytes of one device Model of precision prec, and its host image.
 size_t model_bytes(int prec);
 void model_image(int prec, const HostModel& hm, void* out);

@@ -53,6 +53,12 @@ Model<R> make_model(const HostModel& h) {
   m.w0_mode = h.w0_mode;
   m.coupling = h.coupling;
   m.stream_id = h.stream_id;
+  m.qoi1_mode = h.qoi1_mode;
+  m.sdeg = h.smooth_r + 1;
+  m.qa = (R)h.qa;
+  m.qb = (R)h.qb;
+  m.idelta = h.qoi1_mode ? (R)(1.0 / h.delta) : R(0);
+  for (int k = 0; k < 12; ++k) m.pc[k] = (R)h.pc[k];
   for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
   return m;
 }
@@ -79,10 +85,18 @@ Level<R> make_level(const LevelSpec& s) {
 // terms, error below 1e-12 relative); the compensation is applied where the
 // partial sums of a block and of the blocks are combined.  On the coarsest
 // level P_c = 0, so only sum Y and sum Y^2 are kept (sum P_f = sum Y).
+// QoI 1: the indicator is counted in integers (exact); the smoothed
+// interval QoI keeps its six FP64 sums per thread in shared memory (they are
+// touched once per path), so it costs no registers when unused.
 struct Acc {
   double y, y2, pf, pf2, pc, pc2;
   uint32_t n, bad, nf, nc, nd;
 };
+
+__device__ __forceinline__ double (*q1_smem())[kBlock] {
+  __shared__ double s_q1[6][kBlock];
+  return s_q1;
+}
 
 __device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
   const double y = x - c;
@@ -91,14 +105,18 @@ __device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
   s = t;
 }
 
-__device__ __forceinline__ void acc_zero(Acc& a) {
+__device__ __forceinline__ void acc_zero(Acc& a, bool smooth) {
   a.y = a.y2 = a.pf = a.pf2 = a.pc = a.pc2 = 0.0;
   a.n = a.bad = a.nf = a.nc = a.nd = 0;
+  if (smooth) {
+    double (*q)[kBlock] = q1_smem();
+    for (int k = 0; k < 6; ++k) q[k][threadIdx.x] = 0.0;
+  }
 }
 
-// QoIs at T (Section 3.2): P = z(T) and P = 1[z(T) < threshold]; Y = P_f -
-// P_c is formed in FP64 (exact for two floats); the indicator decision is
-// taken in the path precision.
+// QoIs at T (Section 3.2): P = z(T), and P = 1[z(T) < threshold] or the
+// smoothed interval; Y = P_f - P_c is formed in FP64 (exact for two floats);
+// the indicator decision is taken in the path precision.
 template <typename R, bool COUPLED>
 __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, bool bad) {
   if (bad) { a.bad += 1; return; }
@@ -116,45 +134,70 @@ __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, b
     a.y += Pf;
     a.y2 = fma(Pf, Pf, a.y2);
   }
-  const bool If = zf < m.qthr;
-  const bool Ic = COUPLED && (zc < m.qthr);
-  a.nf += If; a.nc += Ic; a.nd += (If != Ic);
+  if (m.qoi1_mode) {
+    const double Sf = (double)smoothed_interval(m, zf);
+    const double Sc = COUPLED ? (double)smoothed_interval(m, zc) : 0.0;
+    const double Y1 = Sf - Sc;
+    double (*q)[kBlock] = q1_smem();
+    const int t = threadIdx.x;
+    q[0][t] += Y1;
+    q[1][t] = fma(Y1, Y1, q[1][t]);
+    q[2][t] += Sf;
+    q[3][t] = fma(Sf, Sf, q[3][t]);
+    q[4][t] += Sc;
+    q[5][t] = fma(Sc, Sc, q[5][t]);
+  } else {
+    const bool If = zf < m.qthr;
+    const bool Ic = COUPLED && (zc < m.qthr);
+    a.nf += If; a.nc += Ic; a.nd += (If != Ic);
+  }
   a.n += 1;
 }
 
 // Warp tree (fixed order), then lane 0 of warp 0 adds the warp results in
 // warp order with Kahan compensation.  Ends with the block synchronised.
-__device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled,
+__device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, bool smooth,
                                                    Partial* __restrict__ out) {
-  __shared__ double s_v[kBlock / 32][6];
-  __shared__ unsigned long long s_u[kBlock / 32][5];
-  double v[6] = {a.y, a.y2, coupled ? a.pf : a.y, coupled ? a.pf2 : a.y2, a.pc, a.pc2};
-  unsigned long long u[5] = {a.n, a.bad, a.nf, a.nc, a.nd};
+  __shared__ double s_v[kBlock / 32][12];
+  __shared__ unsigned long long s_u[kBlock / 32][2];
+  double v[12] = {a.y, a.y2, coupled ? a.pf : a.y, coupled ? a.pf2 : a.y2, a.pc, a.pc2};
+  if (smooth) {
+    double (*q)[kBlock] = q1_smem();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[6 + k] = q[k][threadIdx.x];
+  } else {
+    const double nf = (double)a.nf, nc = (double)a.nc, nd = (double)a.nd;
+    v[6] = nf - nc; v[7] = nd; v[8] = nf; v[9] = nf; v[10] = nc; v[11] = nc;
+  }
+  unsigned long long u[2] = {a.n, a.bad};
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+    for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    for (int k = 0; k < 2; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s_v[warp][k] = v[k];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) s_u[warp][k] = u[k];
+    for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
+    s_u[warp][0] = u[0];
+    s_u[warp][1] = u[1];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
-    unsigned long long t[5] = {0, 0, 0, 0, 0};
+    double s[12], c[12];
+    for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
+    unsigned long long t0 = 0, t1 = 0;
     for (int w = 0; w < kBlock / 32; ++w) {
-      for (int k = 0; k < 6; ++k) kahan_add(s[k], c[k], s_v[w][k]);
-      for (int k = 0; k < 5; ++k) t[k] += s_u[w][k];
+      for (int k = 0; k < 12; ++k) kahan_add(s[k], c[k], s_v[w][k]);
+      t0 += s_u[w][0];
+      t1 += s_u[w][1];
     }
-    for (int k = 0; k < 6; ++k) out->s[k] = s[k] - c[k];
-    out->n = t[0]; out->bad = t[1]; out->nf = t[2]; out->nc = t[3]; out->nd = t[4];
-    for (int k = 0; k < 5; ++k) out->pad[k] = 0;
+    for (int k = 0; k < 6; ++k) out->s0[k] = s[k] - c[k];
+    for (int k = 0; k < 6; ++k) out->s1[k] = s[6 + k] - c[6 + k];
+    out->n = t0;
+    out->bad = t1;
   }
   __syncthreads();
 }
@@ -173,7 +216,7 @@ struct SumsArgs {
 template <int INTEG, typename R, bool COUPLED>
 __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
   Acc acc;
-  acc_zero(acc);
+  acc_zero(acc, a.m.qoi1_mode != 0);
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < a.N; j += stride) {
     Path<R> f, c;
@@ -181,7 +224,7 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_level_sums(const __grid_c
     run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
     acc_add<R, COUPLED>(acc, a.m, f.z, c.z, bad);
   }
-  block_reduce_store(acc, COUPLED, a.partials + blockIdx.x);
+  block_reduce_store(acc, COUPLED, a.m.qoi1_mode != 0, a.partials + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -234,13 +277,13 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel(const __grid_c
     const uint64_t left = rq.count - start;
     const uint32_t count = (uint32_t)(left < rq.item_paths ? left : rq.item_paths);
     Acc acc;
-    acc_zero(acc);
+    acc_zero(acc, a.m.qoi1_mode != 0);
     const Level<R> lv = rq.lv;   // registers, not parameter-space loads per step
     if (lv.coupled)
       multilevel_item<INTEG, R, true>(a.m, lv, rq.first + start, count, acc);
     else
       multilevel_item<INTEG, R, false>(a.m, lv, rq.first + start, count, acc);
-    block_reduce_store(acc, lv.coupled != 0, a.partials + it);
+    block_reduce_store(acc, lv.coupled != 0, a.m.qoi1_mode != 0, a.partials + it);
   }
 }
 
@@ -282,12 +325,12 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
     const uint64_t left = pr.count - start;
     const uint32_t count = (uint32_t)(left < pr.item_paths ? left : pr.item_paths);
     Acc acc;
-    acc_zero(acc);
+    acc_zero(acc, m.qoi1_mode != 0);
     if (pr.coupled)
       multilevel_item<INTEG, R, true>(m, rq.lv, pr.first + start, count, acc);
     else
       multilevel_item<INTEG, R, false>(m, rq.lv, pr.first + start, count, acc);
-    block_reduce_store(acc, pr.coupled != 0, partials + it);
+    block_reduce_store(acc, pr.coupled != 0, m.qoi1_mode != 0, partials + it);
   }
 }
 
@@ -336,14 +379,87 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB)
     const uint64_t left = pr.count - start;
     const uint32_t count = (uint32_t)(left < pr.item_paths ? left : pr.item_paths);
     Acc acc;
-    acc_zero(acc);
+    acc_zero(acc, m.qoi1_mode != 0);
     if (pr.coupled)
       multilevel_item<INTEG, R, true>(m, lv, pr.first + start, count, acc);
     else
       multilevel_item<INTEG, R, false>(m, lv, pr.first + start, count, acc);
-    block_reduce_store(acc, pr.coupled != 0, partials + it);
+    block_reduce_store(acc, pr.coupled != 0, m.qoi1_mode != 0, partials + it);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Binned density (Section 5.3, Eq. vector_QoI): k bins [i w, (i+1) w),
+// w = H / k, each QoI the smoothed interval of its bin.  With edge values
+// G_e = g_r((z - e w) / delta), bin i's QoI is G_{i+1} - G_i.  Per thread the
+// sums of Y_i and Y_i^2 sit in dynamic shared memory ([2k][256] doubles);
+// each block writes 2k + 2 doubles (the sums, then the finite and the
+// diverged pair counts) to its own slot.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PdfArgs {
+  Model<R> m;
+  Level<R> lv;
+  uint64_t N, offset;
+  int32_t k;
+  R binw;
+  double* partials;   // gridDim.x x (2k + 2)
+};
+
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock) k_level_pdf(const __grid_constant__ PdfArgs<R> a) {
+  extern __shared__ double s_pdf[];   // [2k][kBlock]
+  const int t = threadIdx.x;
+  const int k = a.k;
+  for (int c = 0; c < 2 * k; ++c) s_pdf[c * kBlock + t] = 0.0;
+  double n_ok = 0.0, n_bad = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + t; j < a.N; j += stride) {
+    Path<R> f, c;
+    bool bad;
+    run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
+    if (bad) { n_bad += 1.0; continue; }
+    n_ok += 1.0;
+    R gf0 = g_smooth(a.m, f.z * a.m.idelta);
+    R gc0 = COUPLED ? g_smooth(a.m, c.z * a.m.idelta) : R(0);
+    for (int i = 0; i < k; ++i) {
+      const R e = (R)(i + 1) * a.binw;
+      const R gf1 = g_smooth(a.m, (f.z - e) * a.m.idelta);
+      const R gc1 = COUPLED ? g_smooth(a.m, (c.z - e) * a.m.idelta) : R(0);
+      const double Y = ((double)gf1 - (double)gf0) - (COUPLED ? ((double)gc1 - (double)gc0) : 0.0);
+      s_pdf[(2 * i) * kBlock + t] += Y;
+      s_pdf[(2 * i + 1) * kBlock + t] = fma(Y, Y, s_pdf[(2 * i + 1) * kBlock + t]);
+      gf0 = gf1;
+      gc0 = gc1;
+    }
+  }
+  // block reduction of each column: warp tree, then warp-ordered Kahan
+  __shared__ double s_w[kBlock / 32];
+  const int lane = t & 31, warp = t >> 5;
+  double* out = a.partials + (size_t)blockIdx.x * (2 * k + 2);
+  for (int col = 0; col < 2 * k + 2; ++col) {
+    double v = col < 2 * k ? s_pdf[col * kBlock + t] : (col == 2 * k ? n_ok : n_bad);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0, cc = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, cc, s_w[w]);
+      out[col] = s - cc;
+    }
+    __syncthreads();
+  }
+}
+
+template <int I, typename R, bool C>
+struct PdfK {
+  static void launch(dim3 g, const PdfArgs<R>& a, cudaStream_t st) {
+    const size_t smem = (size_t)2 * a.k * kBlock * sizeof(double);
+    cudaFuncSetAttribute(k_level_pdf<I, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_level_pdf<I, R, C><<<g, kBlock, smem, st>>>(a);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Per-path outputs
@@ -458,6 +574,10 @@ cudaError_t multilevel_impl(int integ, const HostModel& hm, const ReqPlan* plan,
 }
 
 template <typename R>
+cudaError_t pdf_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
+                     uint64_t offset, int k, double* partials, int grid, cudaStream_t st);
+
+template <typename R>
 cudaError_t multilevel_dev_impl(int integ, const HostModel& hm, const DevPlan* plan,
                                 Partial* partials, unsigned int* counter, int grid,
                                 cudaStream_t st) {
@@ -483,6 +603,20 @@ cudaError_t multilevel_table_impl(int integ, const void* models, size_t stride, 
     k_multilevel_table<kBAOAB, R><<<grid, kBlock, 0, st>>>(mm, stride, reqs, n_req, n_items,
                                                            partials, counter);
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t pdf_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
+                     uint64_t offset, int k, double* partials, int grid, cudaStream_t st) {
+  PdfArgs<R> a;
+  a.m = make_model<R>(hm);
+  a.lv = make_level<R>(ls);
+  a.N = N;
+  a.offset = offset;
+  a.k = k;
+  a.binw = (R)(hm.H / (double)k);
+  a.partials = partials;
+  return launch3<R, PdfK>(integ, ls.coupled, dim3(grid), a, st);
 }
 
 template <typename R>
