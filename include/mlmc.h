@@ -167,6 +167,12 @@ int mlmc_set_tuning(int integrator, int precision, int variant, int items_per_bl
                     int blocks_per_sm);
 int mlmc_get_tuning(int integrator, int precision, int32_t out[3]);
 
+/* Smallest level of the hierarchy on which `integrator` is stable for this
+ * scenario: for symplectic Euler the first l with h_l lambda_max < 2
+ * (Section 3.1, h < 2 / lambda(X); lambda is largest at the regularisation
+ * height), else 0.  Pure host computation; MLMC_EINVAL for bad parameters. */
+int mlmc_stable_level_min(const mlmc_params* p, int integrator, int32_t* level);
+
 /* Bytes of device workspace that every entry point below needs for a batch
  * of up to `max_requests` level requests (1 for single-level calls).  The
  * workspace must be 256-byte aligned.  Pure host computation. */

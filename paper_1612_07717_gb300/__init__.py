@@ -107,6 +107,7 @@ def lib():
                                           C.POINTER(u64), C.POINTER(u64)]
         L.mlmc_estimate_pdf.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, vp,
                                         C.c_size_t, vp, C.POINTER(C.c_double), C.POINTER(Result)]
+        L.mlmc_stable_level_min.argtypes = [C.POINTER(Params), i32, C.POINTER(C.c_int32)]
         L.mlmc_set_tuning.argtypes = [i32, i32, i32, i32, i32]
         L.mlmc_get_tuning.argtypes = [i32, i32, C.POINTER(C.c_int32)]
         L.mlmc_server_workspace_bytes.restype = C.c_size_t
@@ -151,6 +152,14 @@ def make_params(d=None, **kw):
             if k in _PARAM_FIELDS:
                 setattr(p, k, v)
     return p
+
+
+def stable_level_min(params, integrator):
+    """Smallest stable level of the hierarchy (symplectic Euler: h lambda_max < 2)."""
+    out = C.c_int32()
+    _check(lib().mlmc_stable_level_min(C.byref(params), integrator, C.byref(out)),
+           "mlmc_stable_level_min")
+    return out.value
 
 
 def device_info():

@@ -550,6 +550,23 @@ int mlmc_device_info(int32_t out[3]) {
   return MLMC_OK;
 }
 
+int mlmc_stable_level_min(const mlmc_params* p, int integrator, int32_t* level) {
+  if (!level || integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, 0, &hm);
+  if (rc) return rc;
+  *level = 0;
+  if (integrator != MLMC_SE) return MLMC_OK;
+  const double lam = lambda_max(hm);
+  for (int l = 0; l <= 40; ++l) {
+    if (lam * (p->T / (double)((int64_t)p->M0 << l)) < 2.0) {
+      *level = l;
+      return MLMC_OK;
+    }
+  }
+  return MLMC_EINVAL;
+}
+
 size_t mlmc_workspace_bytes(const mlmc_params* p, int max_requests) {
   (void)p;
   (void)max_requests;

@@ -57,7 +57,7 @@ Model<R> make_model(const HostModel& h) {
   m.sdeg = h.smooth_r + 1;
   m.qa = (R)h.qa;
   m.qb = (R)h.qb;
-  m.idelta = h.qoi1_mode ? (R)(1.0 / h.delta) : R(0);
+  m.idelta = h.delta > 0.0 ? (R)(1.0 / h.delta) : R(0);
   for (int k = 0; k < 12; ++k) m.pc[k] = (R)h.pc[k];
   for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
   return m;
