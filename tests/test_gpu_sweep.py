@@ -75,9 +75,10 @@ def test_well_mixed_state_over_1e8_paths():
 
 
 def test_cost_scaling_with_tolerance_in_paper_scenario():
-    d = dict(W.PAPER, L_max=12, n_init=5000)
+    d = dict(W.PAPER, L_max=12, n_init=2000)
     p = G.make_params(d)
-    eps_list = [4e-3, 2e-3, 1e-3, 5e-4]
+    # tight enough that N_l, not the n_init floor, sets the cost
+    eps_list = [8e-4, 4e-4, 2e-4, 1e-4]
     mlmc, stmc = [], []
     for eps in eps_list:
         r = G.estimate_graph(eps, G.GL, p, 23)
