@@ -143,6 +143,8 @@ int orc_normalise(orc_params* p) {
   }
   if (!(p->eps_reg_frac > 0.0) || !(p->eps_reg_frac <= 0.5)) return -1;
   if (!(p->T > 0.0) || p->M0 < 1 || p->level_min < 0) return -1;
+  if (p->z_adapt < 0.0 || p->z_adapt > p->H) return -1;
+  if (p->z_adapt > 0.0 && p->M0 > (1 << 22)) return -1;  /* T in ticks below 2^62 */
   return 0;
 }
 
@@ -244,7 +246,7 @@ static void step_post(int integ, const orc_params* p, state_t* s, double h, doub
 
 /* ------------------------------------------------------------------------ */
 /* Initial state.  w0_mode 0: (z0, w0) as given (the paper's fixed release, */
-/* Section 5).  1: U0 ~ N(0, sigma_U(z0)^2).  2: the well-mixed state,      */
+/* Section 6).  1: U0 ~ N(0, sigma_U(z0)^2).  2: the well-mixed state,      */
 /* X0 ~ U(0, H) and U0 | X0 ~ N(0, sigma_U(X0)^2) (Section 2).  The random  */
 /* draws use the reserved counter block 0xFFFFFFFF and are shared by the    */
 /* fine and coarse path of a pair.                                          */
@@ -288,6 +290,156 @@ static double normal_at(const orc_params* p, int level, uint64_t i, uint64_t see
   return nc->xi[n % 4];
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adaptive, non-nested timesteps (Section 7.2, "Adaptive timestepping").     */
+/*                                                                          */
+/* Step rule, Eq. (adaptive h): h_n = min(h, lambda(X_adapt) / lambda(X_n) h) */
+/* with X_n the path's own position at the start of its step (lambda of the */
+/* regularised profile), and the last step of a path shortened to end at T. */
+/* Time is counted in ticks of h_0 / 2^40 with h_0 = T / M0, so that h_l =  */
+/* 2^(40 - l) ticks on every level, h_n = floor(ratio h_l) ticks (at least  */
+/* 1) and the fine and coarse time points of a pair are compared exactly.   */
+/*                                                                          */
+/* Coupling on the merged grid tau_0 = 0 < tau_1 < ... < T of the fine and  */
+/* coarse time points: interval j carries the normal xi_j (element j mod 4  */
+/* of Philox block j / 4, the counter the uniform path uses for fine step   */
+/* j).  Over one step of a path the increments of the intervals inside it   */
+/* combine as                                                               */
+/*   SE, Eq. (AdaptivityIncrementEuler):                                    */
+/*     dW = S_i^(c) sum_j S_j^(f) xi_j sqrt(tau_{j+1} - tau_j)               */
+/*   GL, Eq. (AdaptivityIncrementSplitting):                                */
+/*     A = S_i^(c) sum_j S_j^(f) xi_j sqrt((1 - e^{-2 lambda d_j}) / (2 lambda)) */
+/*             exp(-lambda sum_{k > j} d_k),   d_j = tau_{j+1} - tau_j,       */
+/* where dW replaces sqrt(h) xi in Eq. (MethodSymplecticEuler) and A        */
+/* replaces sqrt((1 - e^{-2 lambda h}) / (2 lambda)) xi in the O-step of     */
+/* Eq. (MethodSymplecticEulerOU).  For the fine path the parities are       */
+/* dropped.  S_j^(f) is the fine parity at tau_j (fixed within a fine step),  */
+/* S_i^(c) the coarse parity at the start of the coarse step.  lambda is the  */
+/* stepping path's own lambda at the start of its step (the reading under   */
+/* which A is exactly the OU noise integral over the step, so the coarse    */
+/* path keeps the law of the fine path one level down).                     */
+/* ------------------------------------------------------------------------ */
+#define ORC_TICK_BITS 40
+
+typedef struct {
+  state_t s;
+  coef_t c;        /* coefficients at the start of the current step */
+  int64_t t_end;   /* tick at which the current step ends           */
+  int64_t n;       /* ticks of the current step                     */
+  double A;        /* noise accumulated over the step               */
+  int64_t steps;
+} astep_t;
+
+/* Start a step at tick t: coefficients at X_n, the step rule, the cap at T. */
+static void adapt_begin(const orc_params* p, astep_t* a, double lam_a, int64_t hmax,
+                        int64_t t, int64_t T_ticks, double* tie) {
+  a->c = coefficients(p, a->s.X);
+  const double ratio = lam_a / a->c.lambda;
+  int64_t n = hmax;
+  if (ratio < 1.0) {
+    n = (int64_t)floor(ratio * (double)hmax);
+    if (n < 1) n = 1;
+  }
+  const double m = fabs(ratio - 1.0);
+  if (m < *tie) *tie = m;
+  if (n > T_ticks - t) n = T_ticks - t;
+  a->n = n;
+  a->t_end = t + n;
+  a->A = 0.0;
+}
+
+/* Add the interval of d seconds with normal xi and parity weight w. */
+static void adapt_accumulate(int integ, astep_t* a, double d, double xi, double w) {
+  if (integ == ORC_SE) {
+    a->A += w * sqrt(d) * xi;
+  } else {
+    const double lam = a->c.lambda;
+    a->A = a->A * exp(-lam * d) + w * sqrt(-expm1(-2.0 * lam * d) / (2.0 * lam)) * xi;
+  }
+}
+
+/* Finish the step with its accumulated noise times the parity factor Sx. */
+static void adapt_step(const orc_params* p, int integ, astep_t* a, double h, double Sx) {
+  state_t* s = &a->s;
+  const coef_t* c = &a->c;
+  if (integ == ORC_SE) {
+    double U1 = (1.0 - c->lambda * h) * s->U - dVdX(c, s->U) * h + c->sigma * (Sx * a->A);
+    s->U = U1;
+    s->X = s->X + U1 * h;
+  } else {
+    double Ustar = exp(-c->lambda * h) * s->U + c->sigma * (Sx * a->A);  /* O */
+    double U1 = Ustar - dVdX(c, Ustar) * h;                                /* B */
+    s->U = U1;
+    s->X = s->X + U1 * h;                                                  /* A */
+  }
+  reflect(p, s);
+  a->steps += 1;
+}
+
+static int path_adaptive(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
+                         orc_path_out* out) {
+  if (integ == ORC_BAOAB || level > ORC_TICK_BITS) return -1;
+  const int coupled = level > p->level_min;
+  const double lam_a = coefficients(p, p->z_adapt).lambda;
+  const double h0 = p->T / (double)p->M0;
+  const double sec = ldexp(h0, -ORC_TICK_BITS);           /* seconds per tick */
+  const int64_t T_ticks = (int64_t)p->M0 << ORC_TICK_BITS;
+  const int64_t hf = (int64_t)1 << (ORC_TICK_BITS - level);
+  const int64_t hc = 2 * hf;
+  double tie = 1.0, gap = 1.0;
+
+  astep_t f, c;
+  double X0, U0;
+  initial_state(p, level, i, seed, &X0, &U0);
+  memset(&f, 0, sizeof(f));
+  f.s.X = X0; f.s.U = U0; f.s.S = 1;
+  c = f;
+  adapt_begin(p, &f, lam_a, hf, 0, T_ticks, &tie);
+  if (coupled) adapt_begin(p, &c, lam_a, hc, 0, T_ticks, &tie);
+
+  normal_cache_t nc;
+  nc.block = 0xFFFFFFFFu;
+  int64_t t = 0, j = 0;
+  while (t < T_ticks && !(f.s.bad || (coupled && c.s.bad))) {
+    int64_t t_next = f.t_end;
+    if (coupled) {
+      if (c.t_end < t_next) t_next = c.t_end;
+      if (f.t_end != c.t_end) {
+        const double m = (double)llabs(f.t_end - c.t_end) / (double)hf;
+        if (m < gap) gap = m;
+      }
+    }
+    const double d = (double)(t_next - t) * sec;
+    const double xi = normal_at(p, level, i, seed, &nc, j);
+    j += 1;
+    const double Sf = (p->coupling == 1) ? 1.0 : (double)f.s.S;  /* S_j^(f) at tau_j */
+    adapt_accumulate(integ, &f, d, xi, 1.0);
+    if (coupled) adapt_accumulate(integ, &c, d, xi, Sf);
+    t = t_next;
+    if (t == f.t_end) {
+      adapt_step(p, integ, &f, (double)f.n * sec, 1.0);
+      if (t < T_ticks) adapt_begin(p, &f, lam_a, hf, t, T_ticks, &tie);
+    }
+    if (coupled && t == c.t_end) {
+      const double Sc = (p->coupling == 1) ? 1.0 : (double)c.s.S;  /* S_i^(c) */
+      adapt_step(p, integ, &c, (double)c.n * sec, Sc);
+      if (t < T_ticks) adapt_begin(p, &c, lam_a, hc, t, T_ticks, &tie);
+    }
+  }
+  out->zf = f.s.X; out->wf = f.s.U;
+  out->zc = coupled ? c.s.X : 0.0;
+  out->wc = coupled ? c.s.U : 0.0;
+  out->nonfinite = (f.s.bad || (coupled && c.s.bad)) ? 1 : 0;
+  out->refl_f = f.s.refl;
+  out->refl_c = coupled ? c.s.refl : 0;
+  out->pad_ = 0;
+  out->steps_f = f.steps;
+  out->steps_c = coupled ? c.steps : 0;
+  out->tie = tie;
+  out->gap = gap;
+  return 0;
+}
+
 int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t seed,
              orc_path_out* out, double* trace_f, double* trace_c) {
   orc_params pp = *pin;
@@ -299,6 +451,10 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
   if (steps_on_level(p, level, &M) != 0) return -1;
   const int coupled = level > p->level_min;
   if (coupled && (M % 2) != 0) return -1;
+  if (p->z_adapt > 0.0) {
+    if (trace_f || trace_c) return -1;
+    return path_adaptive(p, integ, level, i, seed, out);
+  }
   const double h = p->T / (double)M;
 
   state_t f, c;
@@ -362,11 +518,15 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
   out->refl_f = f.refl;
   out->refl_c = coupled ? c.refl : 0;
   out->pad_ = 0;
+  out->steps_f = M;
+  out->steps_c = coupled ? M / 2 : 0;
+  out->tie = 1.0;
+  out->gap = 1.0;
   return 0;
 }
 
 /* ------------------------------------------------------------------------ */
-/* Smoothed indicator, Section 4.1 (Eqs. conc, gr, SmoothedIndicator).      */
+/* Smoothed indicator, Section 5.1 (Eqs. conc, gr, SmoothedIndicator).      */
 /* p_r(s) = sum_k c_k s^k, k = 0..r+1, solves                               */
 /*   p(-1) = 1,  p(1) = 0,                                                  */
 /*   int_{-1}^{1} s^j p(s) ds = (-1)^j / (j + 1),  j = 0..r-1,              */
@@ -443,7 +603,7 @@ static double csum_val(const csum_t* a) { return a->s + a->c; }
 #define CHUNK 1024u
 typedef struct {
   csum_t sum[2][6];
-  uint64_t n, bad;
+  uint64_t n, bad, steps;
 } chunk_t;
 
 typedef struct {
@@ -465,6 +625,7 @@ static void run_chunk(const work_t* w, uint64_t chunk, chunk_t* out) {
   for (uint64_t j = a; j < b; ++j) {
     orc_path_out r;
     orc_path(w->p, w->integ, w->level, w->offset + j, w->seed, &r, NULL, NULL);
+    out->steps += (uint64_t)(r.steps_f + r.steps_c);
     if (r.nonfinite) { out->bad++; continue; }
     double Pf[2], Pc[2];
     Pf[0] = r.zf;
@@ -510,7 +671,6 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
   if (integ < ORC_SE || integ > ORC_BAOAB || level < pp.level_min) return -1;
   int64_t M;
   if (steps_on_level(&pp, level, &M) != 0) return -1;
-  const int coupled = level > pp.level_min;
   if (threads < 1) threads = 1;
   if (threads > 256) threads = 256;
   double coef[24];
@@ -519,7 +679,7 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
 
   csum_t tot[2][6];
   memset(tot, 0, sizeof(tot));
-  uint64_t n_ok = 0, n_bad = 0;
+  uint64_t n_ok = 0, n_bad = 0, n_steps = 0;
   const uint64_t n_chunks_all = (N + CHUNK - 1) / CHUNK;
   const uint64_t BATCH = 4096; /* chunks per batch, bounds memory */
   chunk_t* chunks = (chunk_t*)malloc(sizeof(chunk_t) * BATCH);
@@ -548,6 +708,7 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
         for (int j = 0; j < 6; ++j) csum_add(&tot[q][j], csum_val(&chunks[k].sum[q][j]));
       n_ok += chunks[k].n;
       n_bad += chunks[k].bad;
+      n_steps += chunks[k].steps;
     }
   }
   pthread_mutex_destroy(&lock);
@@ -555,7 +716,9 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
   memset(out, 0, sizeof(*out));
   out->n = n_ok;
   out->n_nonfinite = n_bad;
-  out->path_steps = N * (uint64_t)(coupled ? (M + M / 2) : M);
+  /* integrator steps executed, fine + coarse (M + M/2 per pair with
+   * uniform timesteps) */
+  out->path_steps = n_steps;
   for (int q = 0; q < 2; ++q)
     for (int j = 0; j < 6; ++j) out->sum[q][j] = csum_val(&tot[q][j]);
   return 0;
@@ -563,7 +726,7 @@ int orc_level_sums(const orc_params* pin, int integ, int level, uint64_t N,
 
 /* ------------------------------------------------------------------------ */
 /* Adaptive MLMC driver: the algorithm of Giles (2008, Operations Research, */
-/* Section 5) that the paper uses to pick N_l on the fly (Section 5, second */
+/* Section 5) that the paper uses to pick N_l on the fly (Section 6, second */
 /* paragraph):                                                              */
 /*   1. start with L = level_min                                            */
 /*   2. estimate V_L with n_init samples                                    */
@@ -619,8 +782,9 @@ int orc_estimate(const orc_params* pin, int integ, double eps, uint64_t seed,
         double m1 = S[l].sum[0][0], m2 = S[l].sum[0][1];
         V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
         if (V[l] < 0.0) V[l] = 0.0;
-        int64_t M = (int64_t)p->M0 << l;
-        C[l] = (l > lmin) ? (double)(M + M / 2) : (double)M;
+        /* C_l: integrator steps of one sample (measured: fixed with uniform
+         * timesteps, state-dependent with adaptive ones) */
+        C[l] = (double)S[l].path_steps / (double)(S[l].n + S[l].n_nonfinite);
         total += sqrt(V[l] * C[l]);
       }
       for (int l = lmin; l <= L; ++l) {
@@ -665,7 +829,7 @@ int orc_estimate(const orc_params* pin, int integ, double eps, uint64_t seed,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Binned density, Section 5.3 (Eq. vector_QoI): bin i = [a_i, a_{i+1}),    */
+/* Binned density, Section 6.3 (Eq. vector_QoI): bin i = [a_i, a_{i+1}),    */
 /* a_i = i H / k, QoI P_i = P^{r,delta}_{[a_i, a_{i+1}]}(X_T); per bin the   */
 /* six sums of Y_i = P_i(fine) - P_i(coarse).  Same fixed chunk order and    */
 /* Neumaier sums as orc_level_sums.                                         */

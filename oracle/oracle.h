@@ -53,6 +53,8 @@ typedef struct {
   double smooth_delta;  /* smoothing width delta [m]                                 */
   int32_t smooth_r;     /* smoothing order r (p_r has degree r + 1)                  */
   int32_t pad2_;
+  double z_adapt;       /* > 0: adaptive timesteps with reference height X_adapt [m]
+                           (Section 7.2, SE and GL only); 0: uniform timesteps        */
 } orc_params;
 
 typedef struct {
@@ -60,6 +62,12 @@ typedef struct {
   int32_t nonfinite;     /* 1 if either path left |z| <= 1e3 H or became NaN  */
   int32_t refl_f, refl_c;/* number of reflections on each path                */
   int32_t pad_;
+  int64_t steps_f, steps_c; /* integrator steps taken by each path             */
+  double tie;            /* adaptive timesteps: smallest |ratio - 1| of a step
+                            decision (see orc_path); 1 for uniform timesteps */
+  double gap;            /* adaptive timesteps: smallest |t_f - t_c| / h over
+                            distinct next fine and coarse time points; 1 for
+                            uniform timesteps                                */
 } orc_path_out;
 
 /* per QoI q (0: z(T), 1: 1[z(T) < threshold]) the six sums
@@ -100,7 +108,17 @@ int orc_normalise(orc_params* p);
 
 /* One coupled path pair of level `level` (fine only when level ==
  * level_min).  trace_f (3 * (M+1) doubles: z, w, S per fine time point) and
- * trace_c (3 * (M/2+1)) are optional.  Returns 0, or -1 on bad arguments. */
+ * trace_c (3 * (M/2+1)) are optional (uniform timesteps only).  With
+ * p->z_adapt > 0 the pair takes the adaptive, non-nested timesteps of
+ * Section 7.2 on the merged time grid; time is counted in ticks of
+ * h_0 / 2^40 (h_0 = T / M0) and each adaptive step is a whole number of
+ * ticks.  out->tie is the smallest |lambda(X_adapt) / lambda(X_n) - 1| over
+ * the step decisions: where it is tiny, a rounding difference can decide
+ * between a full and a shortened step and so change the number of merged
+ * intervals.  out->gap is the smallest |t_f - t_c| / h over distinct next
+ * fine and coarse time points (a rounding difference there only moves a
+ * short interval between neighbouring steps).  Returns 0, or -1 on bad
+ * arguments. */
 int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
              orc_path_out* out, double* trace_f, double* trace_c);
 
@@ -109,7 +127,7 @@ int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t see
 int orc_level_sums(const orc_params* p, int integ, int level, uint64_t N,
                    uint64_t offset, uint64_t seed, int threads, orc_level_sums_t* out);
 
-/* Smoothing polynomial p_r of Section 4.1: degree r + 1, p(-1) = 1,
+/* Smoothing polynomial p_r of Section 5.1: degree r + 1, p(-1) = 1,
  * p(1) = 0, and its first r moments on [-1, 1] equal those of the step
  * function.  coef[k] multiplies s^k, k = 0..r+1.  Returns 0 or -1. */
 int orc_smooth_poly(int r, double* coef);
@@ -117,7 +135,7 @@ int orc_smooth_poly(int r, double* coef);
 /* g_r(x): 1 for x < -1, p_r(x) on [-1, 1], 0 for x > 1 (Eq. gr). */
 double orc_g(int r, const double* coef, double x);
 
-/* Level sums of the binned density (Section 5.3, Eq. vector_QoI): k bins
+/* Level sums of the binned density (Section 6.3, Eq. vector_QoI): k bins
  * [i H / k, (i + 1) H / k), each QoI the smoothed interval P^{r,delta};
  * out[6 * i + j] as the six sums of orc_level_sums for bin i. */
 int orc_level_pdf_sums(const orc_params* p, int integ, int level, uint64_t N, uint64_t offset,

@@ -27,13 +27,15 @@ class Params(C.Structure):
         ("n_init", C.c_int32), ("uniform_map", C.c_int32), ("stream_id", C.c_uint32),
         ("qoi1_mode", C.c_int32), ("qoi_a", C.c_double), ("qoi_b", C.c_double),
         ("smooth_delta", C.c_double), ("smooth_r", C.c_int32), ("pad2_", C.c_int32),
+        ("z_adapt", C.c_double),
     ]
 
 
 class PathOut(C.Structure):
     _fields_ = [("zf", C.c_double), ("wf", C.c_double), ("zc", C.c_double), ("wc", C.c_double),
                 ("nonfinite", C.c_int32), ("refl_f", C.c_int32), ("refl_c", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("pad_", C.c_int32), ("steps_f", C.c_int64), ("steps_c", C.c_int64),
+                ("tie", C.c_double), ("gap", C.c_double)]
 
 
 class LevelSums(C.Structure):
@@ -85,7 +87,7 @@ _DEFAULTS = dict(u_star=0.2, f_coriolis=1e-4, H=0.0, kappa_sigma=1.3, kappa_tau=
                  eps_reg_frac=1e-3, z0=0.0, w0=0.0, T=1.0, qoi_threshold=0.0, w0_mode=0, M0=8,
                  level_min=0, L_max=10, coupling=0, drift_outside=0, n_init=10000,
                  uniform_map=U32, stream_id=0, qoi1_mode=0, qoi_a=0.0, qoi_b=0.0,
-                 smooth_delta=0.0, smooth_r=4)
+                 smooth_delta=0.0, smooth_r=4, z_adapt=0.0)
 
 
 def make_params(d=None, **kw):
@@ -136,22 +138,31 @@ def path(p, integ, level, i, seed, trace=False):
     if rc != 0:
         raise ValueError("orc_path rejected its arguments")
     out = dict(zf=r.zf, wf=r.wf, zc=r.zc, wc=r.wc, nonfinite=r.nonfinite,
-               refl_f=r.refl_f, refl_c=r.refl_c)
+               refl_f=r.refl_f, refl_c=r.refl_c, steps_f=r.steps_f, steps_c=r.steps_c, tie=r.tie,
+               gap=r.gap)
     if trace:
         out["trace_f"] = tf
         out["trace_c"] = tc
     return out
 
 
-def paths(p, integ, level, N, offset, seed):
-    """Final states of N consecutive path pairs as an (N, 4) array plus flags."""
+def paths(p, integ, level, N, offset, seed, extra=False):
+    """Final states of N consecutive path pairs as an (N, 4) array plus flags;
+    with extra=True also (steps_f, steps_c) per pair and the (tie, gap) margins."""
     zs = np.zeros((N, 4))
     bad = np.zeros(N, dtype=np.int32)
+    steps = np.zeros((N, 2), dtype=np.int64)
+    tie = np.zeros((N, 2))
     r = PathOut()
     for j in range(N):
-        lib().orc_path(C.byref(p), integ, level, offset + j, seed, C.byref(r), None, None)
+        if lib().orc_path(C.byref(p), integ, level, offset + j, seed, C.byref(r), None, None):
+            raise ValueError("orc_path rejected its arguments")
         zs[j] = (r.zf, r.wf, r.zc, r.wc)
         bad[j] = r.nonfinite
+        steps[j] = (r.steps_f, r.steps_c)
+        tie[j] = (r.tie, r.gap)
+    if extra:
+        return zs, bad, steps, tie
     return zs, bad
 
 
