@@ -94,7 +94,7 @@ typedef struct mlmc_params {
   uint32_t stream_id;   /* Philox counter word 3: one random stream per query    */
   int32_t allow_unstable; /* 1: run SE levels with h lambda_max >= 2 anyway      */
   int32_t qoi1_mode;    /* QoI 1: 0 indicator 1[z(T) < qoi_threshold]; 1 smoothed
-                           interval P^{r,delta}_{[qoi_a, qoi_b]}(z(T)) of Section 4.1
+                           interval P^{r,delta}_{[qoi_a, qoi_b]}(z(T)) of Section 5.1
                            (Eq. SmoothedIndicator)                                */
   int32_t smooth_r;     /* smoothing order r, 0..10 (p_r has degree r + 1)      */
   double qoi_a, qoi_b;  /* interval of the smoothed QoI [m], qoi_a < qoi_b       */
@@ -153,8 +153,11 @@ const char* mlmc_strerror(int code);
 int mlmc_device_info(int32_t out[3]);
 
 /* Tuning of the persistent multi-level kernels for one (integrator,
- * precision): `variant` is the register budget the kernel was compiled for,
- * as resident blocks per SM (1 uncapped, 3, or 4; FP64 only 1);
+ * precision): `variant` selects the compiled kernel: 1 (uncapped), 3 or 4
+ * = one path pair per thread, compiled for that many resident blocks per
+ * SM; 12 or 13 = two path pairs per thread on the packed FP32
+ * instructions, compiled for 2 or 3 blocks per SM (FP32 only; per-path
+ * results bit-identical to the one-pair kernels); FP64 only 1;
  * `items_per_block` the planner's work items per resident block (1..1024;
  * smaller items balance better, larger ones reduce per-item overhead);
  * `blocks_per_sm` the resident blocks per SM launched (0 = all that fit).
@@ -180,7 +183,7 @@ size_t mlmc_workspace_bytes(const mlmc_params* p, int max_requests);
 
 /* ------------------------------------------------------------ estimation */
 /* Sums of N coupled pairs of `level` (plain paths on level_min), paths
- * [path_offset, path_offset + N); Section 3.2, Eq. (Yhatell).  Launches the
+ * [path_offset, path_offset + N); Section 3.3, Eq. (Yhatell).  Launches the
  * coupled-level kernel and the fixed-order reduction on `stream`, copies the
  * sums into *out and synchronises the stream.  Returns MLMC_ENONFINITE (with
  * valid *out) if any pair diverged, MLMC_EUNSTABLE for an unstable SE level
@@ -232,8 +235,8 @@ int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req, int 
                                  const mlmc_params* p, uint64_t seed, void* stream,
                                  mlmc_level_result* d_out);
 
-/* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Section 3.2 and the
- * sample-size rule of Giles 2008 the paper adopts in Section 5): levels are
+/* Adaptive MLMC estimate of E[z(T)] to RMSE eps (Section 3.3 and the
+ * sample-size rule of Giles 2008 the paper adopts in Section 6): levels are
  * added from level_min, N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k
  * C_k)), converged when max(|Yhat_{L-1}| / 2, |Yhat_L|) < eps / sqrt(2).
  * Host-driven loop of mlmc_level_sums calls on `stream`. */
@@ -274,14 +277,14 @@ int mlmc_stmc_estimate(double eps, int level, int n_pilot, int integrator,
                        size_t ws_bytes, void* stream, mlmc_result* out);
 
 /* ------------------------------------------------------- binned density */
-/* The concentration field of Section 5.3 (Eq. vector_QoI): k equal bins
+/* The concentration field of Section 6.3 (Eq. vector_QoI): k equal bins
  * [i H / k, (i + 1) H / k), i < k <= 32, each QoI the smoothed interval
  * P^{r,delta} of its bin (order p->smooth_r, width p->smooth_delta > 0).
  * mlmc_level_pdf_sums: N pairs of `level` from path_offset; out[2i] = sum
  *   Y_i, out[2i + 1] = sum Y_i^2 (host array of 2k doubles), *n_ok finite
  *   pairs, *n_nonfinite diverged pairs; synchronises the stream.
  * mlmc_estimate_pdf: adaptive MLMC estimate of the k bin probabilities to
- *   RMSE eps per bin, N_l chosen with max_i Var[Y_{l,i}] (Section 5.3) and
+ *   RMSE eps per bin, N_l chosen with max_i Var[Y_{l,i}] (Section 6.3) and
  *   the bias test applied to every bin; pdf[i] (host, k doubles) gets bin
  *   i's estimate; *out as mlmc_estimate with estimate[0] = sum_i pdf[i],
  *   est_variance[0] the largest per-bin estimator variance, V[l] the largest

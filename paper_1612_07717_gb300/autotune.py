@@ -4,8 +4,9 @@ For each (integrator, precision) it times the batched workload (all levels
 0..12 of the 600 m boundary layer, N_l = n0 * 10^(-l/2)) for every
 combination of
 
-* register-budget variant: the kernel compiled for 1 (uncapped), 3 or 4
-  resident 256-thread blocks per SM -- the block shape the SM runs;
+* kernel variant: one path pair per thread, compiled for 1 (uncapped), 3 or
+  4 resident 256-thread blocks per SM, or two pairs per thread on the packed
+  FP32 instructions (12, 13: compiled for 2 or 3 blocks per SM);
 * items per resident block: how finely the planner splits each level into
   work items, i.e. how many path pairs one thread integrates per item
   (paths per thread = item paths / 256);
@@ -23,7 +24,7 @@ from . import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_FILE = os.path.join(HERE, "tuning_gb300.json")
-VARIANTS = {FP32: (1, 3, 4), FP64: (1,)}
+VARIANTS = {FP32: (1, 3, 4, 12, 13), FP64: (1,)}
 ITEMS_PER_BLOCK = (4, 8, 16, 32, 64)
 
 

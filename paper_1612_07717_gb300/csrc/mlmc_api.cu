@@ -41,11 +41,16 @@ MLMC_DECLARE_ALL(prec_f32)
 MLMC_DECLARE_ALL(prec_f64)
 MLMC_DECLARE_MULTI(prec_f32_b3)
 MLMC_DECLARE_MULTI(prec_f32_b4)
+MLMC_DECLARE_MULTI(prec_f32_x2)
+MLMC_DECLARE_MULTI(prec_f32_x2b3)
 
 // ---------------------------------------------------------------------------
 // Tuning table of the persistent kernels per (integrator, precision):
 // register-budget variant (resident blocks per SM the kernel is compiled
-// for: 1 = uncapped, 3, 4; FP64 has only 1), work items per resident block
+// for: 1 = uncapped, 3, 4; 12 and 13 = two path pairs per thread on the
+// packed FP32 instructions, compiled for 2 or 3 blocks per SM; FP64 has
+// only 1),
+// work items per resident block
 // in the planner, and resident blocks per SM actually launched (0 = as many
 // as fit).  The defaults are the best of a GB300 sweep; the autotuner
 // (paper_1612_07717_gb300/autotune.py) replaces them.
@@ -64,6 +69,9 @@ static Tune tune_of(int prec, int integ) {
 }
 
 int items_per_block(int prec, int integ) { return tune_of(prec, integ).items_per_block; }
+uint64_t min_item_paths(int prec, int integ) {
+  return (uint64_t)kBlock * (tune_of(prec, integ).variant >= 12 ? 2u : 1u);
+}
 
 #define MLMC_DISPATCH_MULTI(prec, integ, CALL)                     \
   do {                                                             \
@@ -71,6 +79,8 @@ int items_per_block(int prec, int integ) { return tune_of(prec, integ).items_per
     switch (tune_of(prec, integ).variant) {                        \
       case 3: return prec_f32_b3::CALL;                            \
       case 4: return prec_f32_b4::CALL;                            \
+      case 12: return prec_f32_x2::CALL;                           \
+      case 13: return prec_f32_x2b3::CALL;                         \
       default: return prec_f32::CALL;                              \
     }                                                              \
   } while (0)
@@ -330,7 +340,7 @@ int level_spec(const HostModel& hm, int level, LevelSpec* ls) {
   return MLMC_OK;
 }
 
-// Smoothing polynomial of Section 4.1: p_r has degree r + 1, p(-1) = 1,
+// Smoothing polynomial of Section 5.1: p_r has degree r + 1, p(-1) = 1,
 // p(1) = 0 and the first r moments of the step function on [-1, 1].  The
 // conditions are invariant under s -> -s, p -> 1 - p, so the unique solution
 // is p(s) = 1/2 - q(s) with q odd: q(s) = sum_{k odd <= r+1} b_k s^k,
@@ -520,7 +530,8 @@ int mlmc_set_tuning(int integrator, int precision, int variant, int items_per_bl
                     int blocks_per_sm) {
   if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
   if (precision != MLMC_FP32 && precision != MLMC_FP64) return MLMC_EINVAL;
-  if (variant != 1 && variant != 3 && variant != 4) return MLMC_EINVAL;
+  if (variant != 1 && variant != 3 && variant != 4 && variant != 12 && variant != 13)
+    return MLMC_EINVAL;
   if (precision == MLMC_FP64 && variant != 1) return MLMC_EINVAL;
   if (items_per_block < 1 || items_per_block > 1024) return MLMC_EINVAL;
   if (blocks_per_sm < 0 || blocks_per_sm > kMaxBlocksPerSM) return MLMC_EINVAL;
@@ -625,6 +636,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
   // about items_per_block items per resident block, bounded by kMaxItems
   double target = total / ((double)items_per_block(p->precision, integ) * (double)grid);
   if (target < 1.0) target = 1.0;
+  const uint64_t min_paths = min_item_paths(p->precision, integ);
   uint64_t items = 0;
   for (int pass = 0; pass < 40; ++pass) {
     items = 0;
@@ -633,7 +645,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       LevelSpec ls;
       level_spec(hm, q.level, &ls);
       double ppi = std::floor(target / (double)steps_per_pair(ls));
-      uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+      uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
       if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
       const uint64_t n_it = q.count ? (q.count + item_paths - 1) / item_paths : 0;
       plan[k].lv = ls;
@@ -953,6 +965,7 @@ static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int
   }
   double target = total / (16.0 * (double)grid);
   if (target < 1.0) target = 1.0;
+  const uint64_t min_paths = min_item_paths(p->precision, integ);
   for (int pass = 0; pass < 64; ++pass) {
     uint64_t items = 0;
     bool too_big = false;
@@ -960,7 +973,7 @@ static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int
       LevelSpec ls;
       level_spec(hm, reqs[k].level, &ls);
       const double ppi = std::floor(target / (double)steps_per_pair(ls));
-      uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+      uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
       if (item_paths > 0x7FFFFFFFull) { item_paths = 0x7FFFFFFFull; too_big = true; }
       const uint64_t n_it = reqs[k].count ? (reqs[k].count + item_paths - 1) / item_paths : 0;
       plan[k].lv = ls;

@@ -219,7 +219,7 @@ __device__ __forceinline__ void drift_coef(const Model<R>& m, R z, R& g0, R& g1)
 }
 
 // ---------------------------------------------------------------------------
-// Smoothed indicator (Section 4.1, Eqs. gr and SmoothedIndicator):
+// Smoothed indicator (Section 5.1, Eqs. gr and SmoothedIndicator):
 // g_r(x) = 1 for x < -1, p_r(x) on [-1, 1], 0 for x > 1, and
 // P^{r,delta}_{[a,b]}(z) = g_r((z - b) / delta) - g_r((z - a) / delta).
 // ---------------------------------------------------------------------------
@@ -433,7 +433,7 @@ struct Trace {
 };
 
 // ---------------------------------------------------------------------------
-// One path pair of a level (Section 3.2): fine path with M steps and, on
+// One path pair of a level (Section 3.3): fine path with M steps and, on
 // coupled levels, the coarse path with M/2 steps driven by the same Brownian
 // increments.  Normal n of the fine path is word n mod 4 of Philox block n/4.
 // With EX = false the reflections are the fast single fold and `flag`

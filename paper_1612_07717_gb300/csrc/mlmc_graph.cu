@@ -1,5 +1,5 @@
 // mlmc_graph.cu -- the adaptive MLMC loop (Giles 2008, Section 5, the rule
-// the paper adopts in its Section 5) run entirely on the device as one CUDA
+// the paper adopts in its Section 6) run entirely on the device as one CUDA
 // graph: an init kernel, then a conditional WHILE node whose body is
 //   persistent multi-level kernel -> per-request reduction -> update kernel.
 // The update kernel folds the new sums into the per-level totals, applies
@@ -21,6 +21,7 @@ constexpr int kMaxIterations = 4 * kLevels;  // a driver pass count that cannot 
 struct GState {
   int32_t L, pass, iter, converged, status, lmin, Lmax, n_init;
   int32_t M0, grid, done, items_per_block;
+  int32_t min_item, pad_;
   double eps, T;
   uint64_t Ndone[kLevels], dN[kLevels];
   uint64_t n[kLevels], bad[kLevels], steps[kLevels];
@@ -55,7 +56,7 @@ __device__ void plan_device(const GState* g, DevPlan* plan) {
       if (!g->dN[l]) continue;
       const uint64_t spp = dev_steps(g, l);
       const double ppi = floor(target / (double)spp);
-      uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+      uint64_t item_paths = ppi < (double)g->min_item ? (uint64_t)g->min_item : (uint64_t)ppi;
       if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
       const uint64_t n_it = (g->dN[l] + item_paths - 1) / item_paths;
       PlanReq& q = plan->req[k++];
@@ -107,7 +108,7 @@ __device__ void write_result(const GState* g, mlmc_result* out) {
 }
 
 __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, int Lmax, int n_init,
-                             int M0, int grid, int ipb, double eps, double T) {
+                             int M0, int grid, int ipb, int min_item, double eps, double T) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   GState* g = &r->g;
   memset(g, 0, sizeof(*g));
@@ -117,6 +118,7 @@ __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, in
   g->M0 = M0;
   g->grid = grid;
   g->items_per_block = ipb;
+  g->min_item = min_item;
   g->eps = eps;
   g->T = T;
   g->L = lmin;
@@ -261,7 +263,8 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
   CK(cudaStreamBeginCaptureToGraph(g->cap, g->graph, nullptr, nullptr, 0,
                                    cudaStreamCaptureModeThreadLocal));
   k_graph_init<<<1, 32, 0, g->cap>>>(g->region, w.counter, p->level_min, p->L_max, p->n_init,
-                                     p->M0, grid, items_per_block(prec, integrator), eps, p->T);
+                                     p->M0, grid, items_per_block(prec, integrator),
+                                     (int)min_item_paths(prec, integrator), eps, p->T);
   CK(cudaGetLastError());
   CK(cudaStreamEndCapture(g->cap, &g->graph));
   CK(cudaGraphGetNodes(g->graph, &init_node, &n_nodes));

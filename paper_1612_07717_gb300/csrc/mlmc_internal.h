@@ -30,11 +30,11 @@ struct HostModel {
   int32_t w0_mode, coupling, drift_outside, M0, level_min;
   uint32_t stream_id;
   uint32_t rk0[10], rk1[10];
-  int32_t qoi1_mode, smooth_r;        // smoothed interval QoI (Section 4.1)
+  int32_t qoi1_mode, smooth_r;        // smoothed interval QoI (Section 5.1)
   double qa, qb, delta;
   double pc[kMaxSmoothR + 2];         // p_r(s) = sum_k pc[k] s^k
 };
-// Coefficients of the smoothing polynomial p_r (Section 4.1); 0 or -1.
+// Coefficients of the smoothing polynomial p_r (Section 5.1); 0 or -1.
 int smooth_coefficients(int r, double* c);
 
 struct LevelSpec {
@@ -101,6 +101,9 @@ cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSp
 // and tuning table), and the planner's work items per resident block.
 int blocks_per_sm(int prec, int integ, bool multilevel);
 int items_per_block(int prec, int integ);
+// Smallest work item of the planners: one pass of the block over its path
+// pairs (kBlock pairs, 2 kBlock for the two-pairs-per-thread variants).
+uint64_t min_item_paths(int prec, int integ);
 
 // Device facts, workspace carving and parameter handling (mlmc_api.cu).
 struct DevInfo {

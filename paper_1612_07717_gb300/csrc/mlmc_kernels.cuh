@@ -11,8 +11,13 @@
 //   k_paths       final states per pair (validation and per-particle output)
 //   k_trace       full trajectories (validation)
 #pragma once
+#include <type_traits>
+
 #include "mlmc_device.cuh"
 #include "mlmc_internal.h"
+#if MLMC_X2
+#include "mlmc_device_x2.cuh"
+#endif
 
 // Minimum resident blocks per SM requested from the register allocator for
 // the path kernels (1: no register cap).  Each translation unit that
@@ -23,6 +28,11 @@
 #endif
 #ifndef MLMC_KNS
 #define MLMC_KNS kdefault
+#endif
+// MLMC_X2 = 1: the FP32 persistent multi-level kernels run two path pairs
+// per thread on the packed FP32 instructions (mlmc_device_x2.cuh).
+#ifndef MLMC_X2
+#define MLMC_X2 0
 #endif
 
 namespace mlmc {
@@ -114,7 +124,7 @@ __device__ __forceinline__ void acc_zero(Acc& a, bool smooth) {
   }
 }
 
-// QoIs at T (Section 3.2): P = z(T), and P = 1[z(T) < threshold] or the
+// QoIs at T (Section 3.3): P = z(T), and P = 1[z(T) < threshold] or the
 // smoothed interval; Y = P_f - P_c is formed in FP64 (exact for two floats);
 // the indicator decision is taken in the path precision.
 template <typename R, bool COUPLED>
@@ -247,9 +257,49 @@ struct MultiArgs {
   unsigned int* counter;
 };
 
+#if MLMC_X2
+// Lane of a packed pair: the exact replay where the fast pass flagged a
+// multi-layer step, then the finiteness check, exactly as run_pair does.
+template <int INTEG, bool COUPLED>
+__device__ __forceinline__ void finish_lane(const Model<float>& m, const Level<float>& lv,
+                                            uint64_t i, float fz, float fw, float cz, float cw,
+                                            bool multi, Acc& acc) {
+  bool bad = false;
+  if (multi) {
+    Path<float> f, c;
+    run_pair_impl<INTEG, float, COUPLED, true>(m, lv, i, f, c, bad, NoTrace<float>());
+    fz = f.z; fw = f.w; cz = c.z; cw = c.w;
+  }
+  bad |= !(isfinite(fz) && isfinite(fw));
+  if (COUPLED) bad |= !(isfinite(cz) && isfinite(cw));
+  acc_add<float, COUPLED>(acc, m, fz, cz, bad);
+}
+
+// Thread t of the block takes pairs 2t and 2t + 1 of each stride of 2 kBlock
+// pairs; a lane past the item's end is computed and discarded.
+template <int INTEG, bool COUPLED>
+__device__ __forceinline__ void multilevel_item_x2(const Model<float>& m, const Level<float>& lv,
+                                                   uint64_t first, uint32_t count, Acc& acc) {
+  for (uint32_t j = 2 * threadIdx.x; j < count; j += 2 * kBlock) {
+    PathX2 f, c;
+    bool mx, my;
+    run_pair_x2_fast<INTEG, COUPLED>(m, lv, first + j, f, c, mx, my);
+    finish_lane<INTEG, COUPLED>(m, lv, first + j, f.z.x, f.w.x, c.z.x, c.w.x, mx, acc);
+    if (j + 1 < count)
+      finish_lane<INTEG, COUPLED>(m, lv, first + j + 1, f.z.y, f.w.y, c.z.y, c.w.y, my, acc);
+  }
+}
+#endif
+
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
                                                 uint64_t first, uint32_t count, Acc& acc) {
+#if MLMC_X2
+  if constexpr (std::is_same<R, float>::value) {
+    multilevel_item_x2<INTEG, COUPLED>(m, lv, first, count, acc);
+    return;
+  }
+#endif
   for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
     Path<R> f, c;
     bool bad;
@@ -389,7 +439,7 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB)
 }
 
 // ---------------------------------------------------------------------------
-// Binned density (Section 5.3, Eq. vector_QoI): k bins [i w, (i+1) w),
+// Binned density (Section 6.3, Eq. vector_QoI): k bins [i w, (i+1) w),
 // w = H / k, each QoI the smoothed interval of its bin.  With edge values
 // G_e = g_r((z - e w) / delta), bin i's QoI is G_{i+1} - G_i.  Per thread the
 // sums of Y_i and Y_i^2 sit in dynamic shared memory ([2k][256] doubles);

@@ -1,4 +1,4 @@
-// mlmc_pdf.cu -- the binned density of Section 5.3: per-level sums of the
+// mlmc_pdf.cu -- the binned density of Section 6.3: per-level sums of the
 // k smoothed bin QoIs (Eq. vector_QoI) and the adaptive MLMC estimate of the
 // density, whose sample sizes use max_i Var[Y_{l,i}] in place of Var[Y_l]
 // as the paper prescribes for the vector QoI.
@@ -98,7 +98,7 @@ int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params
 }
 
 // Adaptive MLMC estimate of the binned density to RMSE eps per bin: the
-// driver of mlmc_estimate with V_l = max_i Var[Y_{l,i}] (Section 5.3) and the
+// driver of mlmc_estimate with V_l = max_i Var[Y_{l,i}] (Section 6.3) and the
 // bias test applied to every bin, max_i max(|Yhat_{L-1,i}| / 2, |Yhat_{L,i}|)
 // < eps / sqrt(2).  pdf[i] = sum_l Yhat_{l,i}; out->estimate[0] is the total
 // mass sum_i pdf[i], out->est_variance[0] the largest per-bin sum_l V_{l,i}/N_l,

@@ -1,7 +1,7 @@
 // mlmc_serve.cu -- continuous-batching server of dispersion queries.
 //
 // Each query is one adaptive MLMC estimate (Giles 2008, Section 5, the rule
-// the paper adopts in its Section 5) of its own scenario (u*, H, z0, T, eps).
+// the paper adopts in its Section 6) of its own scenario (u*, H, z0, T, eps).
 // A query holds a device slot (its Model) while active.  Every tick the
 // server gathers the pending sample requests of all active queries into one
 // request table, runs ONE persistent multi-level launch over all of them,
@@ -126,12 +126,13 @@ static void q_result(Query& q) {
 }
 
 // Requests of one query for this tick (finest level first).
-static void q_plan(const Query& q, std::vector<PlanReq>& out, uint64_t& items) {
+static void q_plan(const Query& q, uint64_t min_item, std::vector<PlanReq>& out,
+                   uint64_t& items) {
   for (int l = q.L; l >= q.p.level_min; --l) {
     if (!q.dN[l]) continue;
     const uint64_t spp = q_steps(q, l);
     const double ppi = std::floor(kItemTarget / (double)spp);
-    uint64_t item_paths = ppi < (double)kBlock ? (uint64_t)kBlock : (uint64_t)ppi;
+    uint64_t item_paths = ppi < (double)min_item ? min_item : (uint64_t)ppi;
     const uint64_t min_paths = (q.dN[l] + kMaxItemsPerReq - 1) / kMaxItemsPerReq;
     if (item_paths < min_paths) item_paths = min_paths;
     if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
@@ -293,7 +294,7 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
     Query& qq = s->q[id];
     std::vector<PlanReq> mine;
     uint64_t it = 0;
-    q_plan(qq, mine, it);
+    q_plan(qq, min_item_paths(s->prec, s->integ), mine, it);
     if (mine.empty()) continue;
     if (reqs.size() + mine.size() > (size_t)kMaxTableReq || items + it > (uint64_t)kMaxItems) {
       if (reqs.empty()) return MLMC_EWORKSPACE;  // one query alone does not fit

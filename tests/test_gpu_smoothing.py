@@ -1,5 +1,5 @@
 """Smoothed indicator QoI and binned density on the GPU against the oracle
-(Section 4.1 and Section 5.3 of the paper).
+(Section 5.1 and Section 6.3 of the paper).
 
 The GPU evaluates the smoothing polynomial (solved by the library's own
 reduced odd system) in the path precision; the checks are

@@ -5,7 +5,7 @@
 * Well-mixed state over 1e8 paths: the height histogram stays flat and the
   velocity variance stays sigma_w^2, up to a discretisation error that falls
   as the step shrinks (Section 2, the well-mixed condition).
-* Cost against tolerance in the paper's scenario (Section 5.1): MLMC cost
+* Cost against tolerance in the paper's scenario (Section 6.1): MLMC cost
   grows like eps^-2, plain Monte Carlo at the matching step like eps^-3.
 """
 import math

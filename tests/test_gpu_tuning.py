@@ -19,7 +19,7 @@ def test_all_variants_agree(integ):
     ref = [G.level_sums(l, n, integ, p, 9, path_offset=f) for l, f, n in reqs]
     saved = T.get_tuning(integ, G.FP32)
     try:
-        for var in (1, 3, 4):
+        for var in (1, 3, 4, 12, 13):
             for ipb in (4, 64):
                 T.set_tuning(integ, G.FP32, var, ipb, 0)
                 got = G.multilevel_sums(reqs, integ, p, 9)

@@ -5,7 +5,7 @@
 * well-mixed invariance of the model (Section 2);
 * variance decay rates: beta ~ 2 with the reflection-aware coupling, much
   less with the naive coupling (Section 4.1), beta ~ 1 for the indicator;
-* the paper's printed values in its Section 5 scenario;
+* the paper's printed values in its Section 6 scenario;
 * determinism: thread-count independence and path_offset composability;
 * the adaptive driver against Giles' Eq. 12 and its bias test.
 """
@@ -121,7 +121,7 @@ def test_paper_mean_position_and_interval_probability():
 
 def test_bias_ratio_between_integrators_is_paper_like():
     # E[Y_l] = E[P_l - P_{l-1}] estimates the first-order bias at h_l, with
-    # a small variance thanks to the coupling (Section 5.1 bias plot).
+    # a small variance thanks to the coupling (Section 6.1 bias plot).
     p = O.make_params(W.PAPER)
     N = 40000
     means = {}

@@ -1,10 +1,10 @@
 """Pins of the oracle's smoothed indicator and binned density (CPU only),
-Section 4.1 and Section 5.3 of the paper.
+Section 5.1 and Section 6.3 of the paper.
 
 * p_r is symmetric: p(s) + p(-s) = 1 (the step function's defining
   conditions are invariant under s -> -s, 1 - p);
 * g_r turns the step function's expectation into a smooth one with weak
-  error O(delta^{r+1}) (Section 4.1): checked against the normal CDF by
+  error O(delta^{r+1}) (Section 5.2): checked against the normal CDF by
   quadrature, with the convergence rate in delta;
 * the smoothed interval probability of the paper's scenario matches its
   table of estimates for r = 4, delta = 0.1;
