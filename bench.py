@@ -213,6 +213,37 @@ def time_to_eps(G, W, torch, eps_frac=2.0 ** -10):
     return out
 
 
+def adaptive_cost(G, W, torch, eps=1e-4, x_adapt=0.05):
+    """Section 7.3's comparison in the paper's scenario: MLMC to RMSE eps on
+    E[X_T] with uniform and with adaptive timesteps (X_adapt = 0.05), SE and
+    GL, FP32 paths, host-driven estimator; plus the adaptive kernel's
+    throughput on one level against the uniform kernel's."""
+    out = {"eps": eps, "x_adapt": x_adapt, "scenario": "paper (H = 1, T = 1, X0 = 0.05)"}
+    for name, integ in (("se", G.SE), ("gl", G.GL)):
+        row = {}
+        for mode, za in (("uniform", 0.0), ("adaptive", x_adapt)):
+            p = G.make_params(dict(W.PAPER, z_adapt=za, L_max=12), precision=G.FP32)
+            ws = G.Workspace(p)
+            G.estimate(eps * 4, integ, p, 2, workspace=ws)   # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = G.estimate(eps, integ, p, 3, workspace=ws)
+            dt = time.perf_counter() - t
+            level = 6
+            n = 1 << 20
+            G.level_sums(level, n, integ, p, 4, workspace=ws)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s = G.level_sums(level, n, integ, p, 4, workspace=ws)
+            dt1 = time.perf_counter() - t1
+            row[mode] = {"seconds": dt, "L": r["L"], "estimate": r["estimate"][0],
+                         "path_steps": r["total_path_steps"], "converged": r["converged"],
+                         "level6_path_steps_per_s": s["path_steps"] / dt1,
+                         "level6_steps_per_pair": s["path_steps"] / n}
+        out[name] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +252,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-eps", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--n0", type=float, default=N0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -339,6 +371,8 @@ def main():
         }
         if not args.no_time_to_eps:
             out["time_to_eps"] = time_to_eps(G, W, torch)
+        if not args.no_adaptive:
+            out["adaptive_timesteps"] = adaptive_cost(G, W, torch)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(out))

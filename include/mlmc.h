@@ -99,6 +99,16 @@ typedef struct mlmc_params {
   int32_t smooth_r;     /* smoothing order r, 0..10 (p_r has degree r + 1)      */
   double qoi_a, qoi_b;  /* interval of the smoothed QoI [m], qoi_a < qoi_b       */
   double smooth_delta;  /* smoothing width delta [m], > 0 when smoothing is used */
+  double z_adapt;       /* 0: uniform timesteps.  > 0: adaptive, non-nested
+                           timesteps with reference height X_adapt = z_adapt [m]
+                           (Section 7.2): h_n = min(h, lambda(X_adapt) /
+                           lambda(X_n) h) in whole ticks of (T / M0) 2^-40, the
+                           coupled pair driven on the merged time grid.  SE and
+                           GL only; needs 0 < z_adapt <= H, M0 <= 2^22 and
+                           lambda(X_adapt) >= lambda_max / 1024.  Supported by
+                           the level-sums, multi-level, estimate and path
+                           entry points; the graph, server and density entry
+                           points return MLMC_EINVAL for it.                  */
 } mlmc_params;
 
 /* Fill *p with the 600 m neutral boundary-layer scenario: u* = 0.2, f = 1e-4,
@@ -343,9 +353,17 @@ int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_par
                            uint64_t seed, uint64_t path_offset, void* d_states,
                            int32_t* d_flags, void* stream);
 
+/* mlmc_level_paths_async for adaptive timesteps (p->z_adapt > 0, else
+ * MLMC_EINVAL), also writing the integrator steps of each pair: d_steps gets
+ * N x 2 int64 values (fine, coarse; coarse 0 on level_min).  No
+ * synchronisation. */
+int mlmc_level_paths_steps_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                                 uint64_t seed, uint64_t path_offset, void* d_states,
+                                 int32_t* d_flags, int64_t* d_steps, void* stream);
+
 /* Full trajectories of N pairs (meant for small N): d_trace_f gets N x (M+1)
  * x 3 values (z, w, S per fine time point), d_trace_c N x (M/2+1) x 3 (may be
- * NULL on level_min).  No synchronisation. */
+ * NULL on level_min).  Uniform timesteps only.  No synchronisation. */
 int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_params* p,
                           uint64_t seed, uint64_t path_offset, void* d_trace_f,
                           void* d_trace_c, void* stream);

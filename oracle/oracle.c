@@ -144,7 +144,11 @@ int orc_normalise(orc_params* p) {
   if (!(p->eps_reg_frac > 0.0) || !(p->eps_reg_frac <= 0.5)) return -1;
   if (!(p->T > 0.0) || p->M0 < 1 || p->level_min < 0) return -1;
   if (p->z_adapt < 0.0 || p->z_adapt > p->H) return -1;
-  if (p->z_adapt > 0.0 && p->M0 > (1 << 22)) return -1;  /* T in ticks below 2^62 */
+  if (p->z_adapt > 0.0) {
+    if (p->M0 > (1 << 22)) return -1;  /* T in ticks below 2^62 */
+    /* lambda(X_adapt) >= lambda_max / 1024 bounds the steps per path */
+    if (!(1024.0 * coefficients(p, p->z_adapt).lambda >= coefficients(p, 0.0).lambda)) return -1;
+  }
   return 0;
 }
 
@@ -296,9 +300,14 @@ static double normal_at(const orc_params* p, int level, uint64_t i, uint64_t see
 /* Step rule, Eq. (adaptive h): h_n = min(h, lambda(X_adapt) / lambda(X_n) h) */
 /* with X_n the path's own position at the start of its step (lambda of the */
 /* regularised profile), and the last step of a path shortened to end at T. */
+/* lambda decreases with height, so the ratio is below 1 exactly when the   */
+/* clamped X_n lies below X_adapt; the step is then shortened to           */
+/* floor(1024 ratio) / 1024 of h (at least 1/1024, which the parameter     */
+/* check guarantees): the same rule on every level, never longer than the   */
+/* paper's step, and a decision that rounding of lambda rarely flips.       */
 /* Time is counted in ticks of h_0 / 2^40 with h_0 = T / M0, so that h_l =  */
-/* 2^(40 - l) ticks on every level, h_n = floor(ratio h_l) ticks (at least  */
-/* 1) and the fine and coarse time points of a pair are compared exactly.   */
+/* 2^(40 - l) ticks and every step is a whole number of ticks; the fine and */
+/* coarse time points of a pair are compared exactly.                       */
 /*                                                                          */
 /* Coupling on the merged grid tau_0 = 0 < tau_1 < ... < T of the fine and  */
 /* coarse time points: interval j carries the normal xi_j (element j mod 4  */
@@ -334,14 +343,20 @@ typedef struct {
 static void adapt_begin(const orc_params* p, astep_t* a, double lam_a, int64_t hmax,
                         int64_t t, int64_t T_ticks, double* tie) {
   a->c = coefficients(p, a->s.X);
-  const double ratio = lam_a / a->c.lambda;
+  const double H = p->H, eps = p->eps_reg_frac * H;
+  const double Xc = fmin(fmax(a->s.X, eps), H - eps);
   int64_t n = hmax;
-  if (ratio < 1.0) {
-    n = (int64_t)floor(ratio * (double)hmax);
-    if (n < 1) n = 1;
+  double m = fabs(Xc - p->z_adapt) / H;      /* margin of the "below X_adapt" test */
+  if (Xc < p->z_adapt) {
+    const double r = 1024.0 * (lam_a / a->c.lambda);
+    double k = floor(r);
+    const double mk = (r - k < k + 1.0 - r ? r - k : k + 1.0 - r) / 1024.0;
+    if (mk < m) m = mk;                        /* margin of the floor */
+    if (k < 1.0) k = 1.0;
+    if (k > 1024.0) k = 1024.0;
+    n = (int64_t)k * (hmax / 1024);
   }
-  const double m = fabs(ratio - 1.0);
-  if (m < *tie) *tie = m;
+  if (t > 0 && m < *tie) *tie = m;             /* the release point is exact on any side */
   if (n > T_ticks - t) n = T_ticks - t;
   a->n = n;
   a->t_end = t + n;
@@ -378,7 +393,7 @@ static void adapt_step(const orc_params* p, int integ, astep_t* a, double h, dou
 
 static int path_adaptive(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
                          orc_path_out* out) {
-  if (integ == ORC_BAOAB || level > ORC_TICK_BITS) return -1;
+  if (integ == ORC_BAOAB || level > ORC_TICK_BITS - 10) return -1;
   const int coupled = level > p->level_min;
   const double lam_a = coefficients(p, p->z_adapt).lambda;
   const double h0 = p->T / (double)p->M0;

@@ -54,7 +54,9 @@ typedef struct {
   int32_t smooth_r;     /* smoothing order r (p_r has degree r + 1)                  */
   int32_t pad2_;
   double z_adapt;       /* > 0: adaptive timesteps with reference height X_adapt [m]
-                           (Section 7.2, SE and GL only); 0: uniform timesteps        */
+                           (Section 7.2, SE and GL only; needs z_adapt <= H,
+                           M0 <= 2^22 and lambda(X_adapt) >= lambda_max / 1024);
+                           0: uniform timesteps                                 */
 } orc_params;
 
 typedef struct {
@@ -63,7 +65,7 @@ typedef struct {
   int32_t refl_f, refl_c;/* number of reflections on each path                */
   int32_t pad_;
   int64_t steps_f, steps_c; /* integrator steps taken by each path             */
-  double tie;            /* adaptive timesteps: smallest |ratio - 1| of a step
+  double tie;            /* adaptive timesteps: smallest margin of a step
                             decision (see orc_path); 1 for uniform timesteps */
   double gap;            /* adaptive timesteps: smallest |t_f - t_c| / h over
                             distinct next fine and coarse time points; 1 for
@@ -112,10 +114,12 @@ int orc_normalise(orc_params* p);
  * p->z_adapt > 0 the pair takes the adaptive, non-nested timesteps of
  * Section 7.2 on the merged time grid; time is counted in ticks of
  * h_0 / 2^40 (h_0 = T / M0) and each adaptive step is a whole number of
- * ticks.  out->tie is the smallest |lambda(X_adapt) / lambda(X_n) - 1| over
- * the step decisions: where it is tiny, a rounding difference can decide
- * between a full and a shortened step and so change the number of merged
- * intervals.  out->gap is the smallest |t_f - t_c| / h over distinct next
+ * ticks; a shortened step is floor(1024 lambda(X_adapt) / lambda(X_n)) / 1024
+ * of h.  out->tie is the smallest margin of a step decision after the
+ * release: |X_n - X_adapt| / H for "below X_adapt", and the distance of
+ * 1024 lambda(X_adapt) / lambda(X_n) to an integer, over 1024, for the
+ * floor.  Where it is tiny, a rounding difference can change a step and with
+ * it the merged grid.  out->gap is the smallest |t_f - t_c| / h over distinct next
  * fine and coarse time points (a rounding difference there only moves a
  * short interval between neighbouring steps).  Returns 0, or -1 on bad
  * arguments. */

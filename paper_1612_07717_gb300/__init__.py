@@ -39,6 +39,7 @@ class Params(C.Structure):
         ("n_init", C.c_int32), ("precision", C.c_int32), ("stream_id", C.c_uint32),
         ("allow_unstable", C.c_int32), ("qoi1_mode", C.c_int32), ("smooth_r", C.c_int32),
         ("qoi_a", C.c_double), ("qoi_b", C.c_double), ("smooth_delta", C.c_double),
+        ("z_adapt", C.c_double),
     ]
 
 
@@ -60,7 +61,7 @@ class LevelRequest(C.Structure):
                 ("count", C.c_uint64)]
 
 
-assert C.sizeof(Params) == 160 and C.sizeof(LevelResult) == 128
+assert C.sizeof(Params) == 168 and C.sizeof(LevelResult) == 128
 
 
 class MLMCError(RuntimeError):
@@ -122,6 +123,8 @@ def lib():
         L.mlmc_stmc_estimate.argtypes = [C.c_double, i32, i32, i32, C.POINTER(Params), u64, vp,
                                          C.c_size_t, vp, C.POINTER(Result)]
         L.mlmc_level_paths_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
+        L.mlmc_level_paths_steps_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp,
+                                                   vp, vp, vp]
         L.mlmc_path_trace_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
         _lib = L
     return _lib
@@ -365,12 +368,21 @@ def stmc_estimate(eps, level, integrator, params, seed, n_pilot=10000, workspace
     return out
 
 
-def level_paths(level, N, integrator, params, seed, path_offset=0, stream=None):
-    """Final (z_f, w_f, z_c, w_c) of N pairs as an (N, 4) CUDA tensor, plus flags."""
+def level_paths(level, N, integrator, params, seed, path_offset=0, stream=None, steps=False):
+    """Final (z_f, w_f, z_c, w_c) of N pairs as an (N, 4) CUDA tensor, plus flags;
+    with steps=True (adaptive timesteps only) also the (N, 2) int64 step counts."""
     import torch
     dt = torch.float64 if params.precision == FP64 else torch.float32
     states = torch.empty((N, 4), dtype=dt, device="cuda")
     flags = torch.empty(N, dtype=torch.int32, device="cuda")
+    if steps:
+        st = torch.empty((N, 2), dtype=torch.int64, device="cuda")
+        rc = lib().mlmc_level_paths_steps_async(
+            level, N, integrator, C.byref(params), seed, path_offset,
+            C.c_void_p(states.data_ptr()), C.c_void_p(flags.data_ptr()),
+            C.c_void_p(st.data_ptr()), _stream_handle(stream))
+        _check(rc, "mlmc_level_paths_steps_async")
+        return states, flags, st
     rc = lib().mlmc_level_paths_async(level, N, integrator, C.byref(params), seed, path_offset,
                                       C.c_void_p(states.data_ptr()), C.c_void_p(flags.data_ptr()),
                                       _stream_handle(stream))

@@ -19,11 +19,12 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libmlmc.so")
 SOURCES = ["mlmc_api.cu", "mlmc_graph.cu", "mlmc_serve.cu", "mlmc_pdf.cu", "mlmc_kernels_f32.cu",
            "mlmc_kernels_f32_b3.cu", "mlmc_kernels_f32_b4.cu", "mlmc_kernels_f32_x2.cu",
-           "mlmc_kernels_f32_x2b3.cu", "mlmc_kernels_f64.cu"]
+           "mlmc_kernels_f32_x2b3.cu", "mlmc_kernels_f64.cu", "mlmc_adaptive.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 path kernels flush subnormals (no value of the path is subnormal
 # except an exp(-lambda h) that underflows, which is then 0).
-FLAGS = {src: ["-ftz=true"] for src in SOURCES if src.startswith("mlmc_kernels_f32")}
+FLAGS = {src: ["-ftz=true"] for src in SOURCES
+         if src.startswith("mlmc_kernels_f32") or src == "mlmc_adaptive.cu"}
 
 
 def nvcc_path():

@@ -1,0 +1,156 @@
+// mlmc_adaptive.cuh -- adaptive, non-nested timesteps for SE and GL
+// (Section 7.2 of Katsiolides et al., arXiv 1612.07717), device side.
+//
+// Step rule, Eq. (adaptive h): h_n = min(h, lambda(X_adapt) / lambda(X_n) h)
+// with X_n the stepping path's own position at the start of its step.
+// lambda decreases with height, so the ratio is below 1 exactly when the
+// clamped X_n lies below X_adapt; the step is then floor(1024 ratio) / 1024
+// of h (at least 1/1024 by the parameter check): the same rule on every
+// level and never longer than the paper's step.  Time runs in integer ticks
+// of (T / M0) 2^-40, so h_l = 2^(40 - l) ticks, every step is a whole number
+// of ticks, the last step of a path ends exactly at T, and fine and coarse
+// time points of a pair are compared exactly.
+//
+// Coupling on the merged grid: interval j between consecutive fine or
+// coarse time points carries the normal xi_j (element j mod 4 of Philox
+// block j / 4, the counter of fine step j on a uniform grid).  Each path
+// accumulates, for the intervals inside its current step,
+//   SE (Eq. AdaptivityIncrementEuler):
+//     A += S_j^(f) sigma sqrt(d_j) xi_j
+//   GL (Eq. AdaptivityIncrementSplitting, applied recursively):
+//     A  = A e^{-lambda d_j} + S_j^(f) sigma sqrt((1 - e^{-2 lambda d_j}) / (2 lambda)) xi_j
+// with sigma = sigma_w sqrt(2 lambda), lambda the path's own lambda at the
+// start of the step and the parities dropped on the fine path; the step
+// then uses S_i^(c) A (fine path: A) in place of sigma sqrt(h) xi (SE) or of
+// the O-step noise (GL).
+//
+// One loop iteration finishes exactly one step (the fine one first when
+// both end at the same tick), so every lane of a warp runs the same step
+// code whichever path it advances.
+#pragma once
+#include "mlmc_device.cuh"
+
+namespace mlmc {
+
+constexpr uint64_t kNoStep = ~0ull;  // t_end of a path that has reached T
+
+template <typename R>
+struct APath {
+  R z, w, S;
+  R su, lam, g0, g1;  // profile at the start of the current step
+  R h;                // length of the current step [s]
+  R A;                // sigma times the noise increment accumulated so far
+  R E;                // GL: exp(-lambda x the part of the step accumulated so far)
+  uint64_t t_end;     // tick at which the current step ends
+  uint32_t steps;     // steps taken
+};
+
+__device__ __forceinline__ float adiv(float a, float b) { return a * ptx_rcp(b); }
+__device__ __forceinline__ double adiv(double a, double b) { return a / b; }
+
+// Start a step of a path at tick t: the profile at X_n, the step rule, the
+// cap at T.  hmax: h of the path in ticks.
+template <typename R>
+__device__ __forceinline__ void astep_begin(const Model<R>& m, APath<R>& p, uint64_t hmax,
+                                            uint64_t t) {
+  profile(m, p.z, p.su, p.lam, p.g0, p.g1);
+  const R zc = fmin_(fmax_(p.z, m.eps), m.Hme);
+  uint64_t n = hmax;
+  if (zc < m.za) {
+    uint32_t k = (uint32_t)(R(1024) * adiv(m.lam_a, p.lam));  // floor of a positive value
+    k = k < 1u ? 1u : (k > 1024u ? 1024u : k);
+    n = (uint64_t)k * (hmax >> 10);
+  }
+  const uint64_t left = m.T_ticks - t;
+  n = n < left ? n : left;
+  p.h = (R)n * m.sec;
+  p.t_end = t + n;
+  p.A = R(0);
+  p.E = R(1);
+}
+
+// Add an interval of d > 0 seconds with normal xi and parity weight wgt.
+template <int INTEG, typename R>
+__device__ __forceinline__ void accumulate(APath<R>& p, R d, R xi, R wgt) {
+  if (INTEG == kSE) {
+    p.A = fma(wgt * (p.su * sqrt_((R(2) * p.lam) * d)), xi, p.A);
+  } else {
+    R e, om;
+    exp_pair(p.lam * (d * R(1.4426950408889634074)), e, om);
+    p.A = fma(wgt * (p.su * sqrt_(om)), xi, p.A * e);
+    p.E *= e;
+  }
+}
+
+// Finish the current step with noise Sx A, then fold into [0, H].
+template <int INTEG, typename R>
+__device__ __forceinline__ void astep_finish(const Model<R>& m, APath<R>& p, R Sx, bool& bad) {
+  if (INTEG == kSE) {
+    const R acc = fma(-p.lam, p.w, fma(p.g1 * p.w, p.w, p.g0));
+    p.w = fma(Sx, p.A, fma(p.h, acc, p.w));
+  } else {
+    const R us = fma(Sx, p.A, p.E * p.w);             // O
+    p.w = fma(p.h, fma(p.g1 * us, us, p.g0), us);     // B at (X_n, U*)
+  }
+  p.z = fma(p.w, p.h, p.z);                           // A
+  reflect_exact(m, p.z, p.w, p.S, bad);
+  p.steps += 1;
+}
+
+// One path pair of a level with adaptive timesteps (fine only when not
+// COUPLED).  `bad` marks a diverged pair (or one past the step bound).
+template <int INTEG, typename R, bool COUPLED>
+__device__ __forceinline__ void run_pair_adapt(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                               APath<R>& f, APath<R>& c, bool& bad) {
+  const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
+  const uint32_t w2 = i_hi ^ lv.c2;
+  const int level = (int)(lv.c2 >> 24);
+  const uint64_t hf = 1ull << (kTickBits - level), hc = hf << 1;
+  R z0, w0;
+  initial_state(m, lv, i_lo, i_hi, z0, w0);
+  f.z = z0; f.w = w0; f.S = R(1); f.steps = 0;
+  bad = false;
+  astep_begin(m, f, hf, 0);
+  c = f;
+  if (COUPLED) astep_begin(m, c, hc, 0);
+  else c.t_end = kNoStep;
+  // lambda(X_adapt) >= lambda_max / 1024 bounds the steps of a pair by
+  // 1024 (M + M/2) (plus the rounding of each step to whole ticks)
+  const uint64_t cap = 2048ull * (uint64_t)lv.M + 64;
+  uint64_t t = 0;
+  uint32_t j = 0, blk = 0xFFFFFFFFu;
+  R x0 = R(0), x1 = R(0), x2 = R(0), x3 = R(0);
+  for (uint64_t it = 0;; ++it) {
+    const uint64_t tn = f.t_end < c.t_end ? f.t_end : c.t_end;
+    if (tn == kNoStep) break;
+    if (it >= cap) { bad = true; break; }
+    if (tn > t) {                       // the merged interval [t, tn] with xi_j
+      if ((j >> 2) != blk) {
+        blk = j >> 2;
+        const uint4 x = philox10(m.rk0, m.rk1, blk, i_lo, w2, m.stream_id);
+        box_muller(x.x, x.y, x0, x1);
+        box_muller(x.z, x.w, x2, x3);
+      }
+      const uint32_t q = j & 3u;
+      const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
+      const R d = (R)(tn - t) * m.sec;
+      accumulate<INTEG>(f, d, xi, R(1));
+      if (COUPLED) accumulate<INTEG>(c, d, xi, m.coupling ? R(1) : f.S);  // S_j^(f)
+      ++j;
+      t = tn;
+    }
+    const bool fine = f.t_end == t;
+    APath<R> p = fine ? f : c;
+    const R Sx = (fine || m.coupling) ? R(1) : p.S;                        // S_i^(c)
+    astep_finish<INTEG>(m, p, Sx, bad);
+    if (p.t_end == m.T_ticks) p.t_end = kNoStep;
+    else astep_begin(m, p, fine ? hf : hc, t);
+    if (fine) f = p;
+    else c = p;
+    if (bad) break;
+  }
+  bad |= !(isfinite(f.z) && isfinite(f.w));
+  if (COUPLED) bad |= !(isfinite(c.z) && isfinite(c.w));
+}
+
+}  // namespace mlmc

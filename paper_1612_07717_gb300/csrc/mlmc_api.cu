@@ -88,12 +88,16 @@ uint64_t min_item_paths(int prec, int integ) {
 cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                               uint64_t N, uint64_t offset, Partial* partials, int grid,
                               cudaStream_t st) {
+  if (hm.adapt) return launch_adapt_sums(prec, integ, hm, lv, N, offset, partials, grid, st);
   return prec ? prec_f64::level_sums(integ, hm, lv, N, offset, partials, grid, st)
               : prec_f32::level_sums(integ, hm, lv, N, offset, partials, grid, st);
 }
 cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                               int n_req, uint32_t n_items, Partial* partials,
                               unsigned int* counter, int grid, cudaStream_t st) {
+  if (hm.adapt)
+    return launch_adapt_multilevel(prec, integ, hm, plan, n_req, n_items, partials, counter, grid,
+                                   st);
   MLMC_DISPATCH_MULTI(prec, integ,
                       multilevel(integ, hm, plan, n_req, n_items, partials, counter, grid, st));
 }
@@ -119,6 +123,7 @@ void model_image(int prec, const HostModel& hm, void* out) {
 }
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                          uint64_t offset, void* s, int32_t* f, cudaStream_t st) {
+  if (hm.adapt) return launch_adapt_paths(prec, integ, hm, lv, N, offset, s, f, nullptr, st);
   return prec ? prec_f64::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st)
               : prec_f32::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st);
 }
@@ -155,39 +160,41 @@ __device__ __forceinline__ void kadd(double& s, double& c, double x) {
 __device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint32_t end,
                              uint64_t path_steps, mlmc_level_result* __restrict__ out) {
   __shared__ double s_v[kBlock / 32][12];
-  __shared__ unsigned long long s_u[kBlock / 32][2];
+  __shared__ unsigned long long s_u[kBlock / 32][3];
   double s[12], c[12];
   for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
-  unsigned long long u[2] = {0, 0};
+  unsigned long long u[3] = {0, 0, 0};
   for (uint32_t j = begin + threadIdx.x; j < end; j += kBlock) {
     for (int k = 0; k < 6; ++k) kadd(s[k], c[k], p[j].s0[k]);
     for (int k = 0; k < 6; ++k) kadd(s[6 + k], c[6 + k], p[j].s1[k]);
     u[0] += p[j].n;
     u[1] += p[j].bad;
+    u[2] += p[j].steps;
   }
   double v[12];
   for (int k = 0; k < 12; ++k) v[k] = s[k] - c[k];
   for (int off = 16; off > 0; off >>= 1) {
     for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-    for (int k = 0; k < 2; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
     for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
-    for (int k = 0; k < 2; ++k) s_u[warp][k] = u[k];
+    for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t[12], tc[12];
     for (int k = 0; k < 12; ++k) t[k] = tc[k] = 0.0;
-    unsigned long long q[2] = {0, 0};
+    unsigned long long q[3] = {0, 0, 0};
     for (int w = 0; w < kBlock / 32; ++w) {
       for (int k = 0; k < 12; ++k) kadd(t[k], tc[k], s_v[w][k]);
-      for (int k = 0; k < 2; ++k) q[k] += s_u[w][k];
+      for (int k = 0; k < 3; ++k) q[k] += s_u[w][k];
     }
     out->n = q[0];
     out->n_nonfinite = q[1];
-    out->path_steps = path_steps;
+    // fixed step counts come from the host; 0 selects the counted steps
+    out->path_steps = path_steps ? path_steps : q[2];
     out->reserved = 0;
     for (int k = 0; k < 6; ++k) out->sum[0][k] = t[k] - tc[k];
     for (int k = 0; k < 6; ++k) out->sum[1][k] = t[6 + k] - tc[6 + k];
@@ -264,6 +271,14 @@ cudaError_t launch_finalize_multi(const Partial* partials, const ReqPlan* plan, 
 // ---------------------------------------------------------------------------
 // Parameter checks and derived constants
 // ---------------------------------------------------------------------------
+// lambda = 1 / tau of the regularised profile (Eq. profiles with the cut-off
+// of Eq. regularisation): sigma_w(z_c) (1 / z_c + c_f f / u*) / kappa_tau.
+static double lambda_at(const HostModel& hm, double z) {
+  const double zc = std::fmin(std::fmax(z, hm.eps), hm.H - hm.eps);
+  const double sig = hm.A * std::pow(1.0 - zc / hm.H, 0.75);
+  return sig * (1.0 / zc + hm.cfu) * hm.inv_ktau;
+}
+
 int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
   if (!p) return MLMC_EINVAL;
   const double us = p->u_star;
@@ -317,6 +332,18 @@ int make_host_model(const mlmc_params* p, uint64_t seed, HostModel* hm) {
   hm->M0 = p->M0;
   hm->level_min = p->level_min;
   hm->stream_id = p->stream_id;
+  // Adaptive timesteps (Section 7.2): lambda(X_adapt) of the regularised
+  // profile; the bound on lambda_max / lambda(X_adapt) bounds the steps per
+  // path (at most 1024 M per path).
+  if (!(p->z_adapt >= 0.0) || !(p->z_adapt <= H)) return MLMC_EINVAL;
+  hm->adapt = p->z_adapt > 0.0 ? 1 : 0;
+  hm->z_adapt = p->z_adapt;
+  hm->lam_a = 0.0;
+  if (hm->adapt) {
+    if (p->M0 > (1 << 22)) return MLMC_EINVAL;
+    hm->lam_a = lambda_at(*hm, p->z_adapt);
+    if (!(hm->lam_a * 1024.0 >= lambda_at(*hm, 0.0))) return MLMC_EINVAL;
+  }
   // Philox round keys: the key schedule adds the Weyl constants per round.
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
@@ -379,12 +406,7 @@ int smooth_coefficients(int r, double* c) {
 }
 
 // lambda is largest at the regularisation height (it falls with z).
-static double lambda_max(const HostModel& hm) {
-  const double zc = hm.eps;
-  const double s = 1.0 - zc / hm.H;
-  const double sig = hm.A * std::pow(s, 0.75);
-  return sig * (1.0 + hm.cfu * zc) * hm.inv_ktau / zc;
-}
+static double lambda_max(const HostModel& hm) { return lambda_at(hm, hm.eps); }
 
 uint64_t steps_per_pair(const LevelSpec& ls) {
   return ls.coupled ? (uint64_t)(ls.M + ls.M / 2) : (uint64_t)ls.M;
@@ -445,10 +467,22 @@ int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
   return g;
 }
 
+// Adaptive timesteps exist for SE and GL only (Section 7.2); with them every
+// step has h_n lambda(X_n) <= h lambda(X_adapt), so SE's bound uses
+// lambda(X_adapt) in place of lambda_max.
 int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls) {
+  if (hm.adapt && integ == MLMC_BAOAB) return MLMC_EINVAL;
+  if (hm.adapt && ls.level > kTickBits - 10) return MLMC_EINVAL;
   if (integ != MLMC_SE || p->allow_unstable) return MLMC_OK;
   const double hmax = ls.coupled ? 2.0 * ls.h : ls.h;  // the coarse path steps 2h
-  return lambda_max(hm) * hmax < 2.0 ? MLMC_OK : MLMC_EUNSTABLE;
+  const double lam = hm.adapt ? hm.lam_a : lambda_max(hm);
+  return lam * hmax < 2.0 ? MLMC_OK : MLMC_EUNSTABLE;
+}
+
+// Steps of N pairs when they are fixed (uniform timesteps); 0 asks the
+// reduction for the steps the adaptive kernels counted.
+static uint64_t fixed_steps(const HostModel& hm, const LevelSpec& ls, uint64_t N) {
+  return hm.adapt ? 0 : N * steps_per_pair(ls);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA; }
@@ -603,7 +637,7 @@ int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
   if (N > (uint64_t)grid * kBlock * 0x7FFFFFFFull) return MLMC_EINVAL;  // per-thread counters
   rc = cuda_status(launch_level_sums(prec, integrator, hm, ls, N, path_offset, w.partials, grid, st));
   if (rc) return rc;
-  rc = cuda_status(launch_finalize(w.partials, grid, N * steps_per_pair(ls), w.results, st));
+  rc = cuda_status(launch_finalize(w.partials, grid, fixed_steps(hm, ls, N), w.results, st));
   if (rc) return rc;
   rc = cuda_status(cudaMemcpyAsync(out, w.results, sizeof(*out), cudaMemcpyDeviceToHost, st));
   if (rc) return rc;
@@ -654,7 +688,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       plan[k].item_paths = (uint32_t)item_paths;
       plan[k].n_items = (uint32_t)n_it;
       plan[k].item_base = (uint32_t)items;
-      plan[k].path_steps = q.count * steps_per_pair(ls);
+      plan[k].path_steps = fixed_steps(hm, ls, q.count);
       items += n_it;
     }
     if (items <= (uint64_t)kMaxItems) break;
@@ -771,8 +805,9 @@ int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t see
         const double m1 = S[l].sum[0][0], m2 = S[l].sum[0][1];
         V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
         if (V[l] < 0.0) V[l] = 0.0;
-        const int64_t M = (int64_t)p->M0 << l;
-        C[l] = l > lmin ? (double)(M + M / 2) : (double)M;
+        // C_l: integrator steps of one sample, M + M/2 with uniform timesteps
+        // (M on level_min) and the counted mean with adaptive ones
+        C[l] = (double)S[l].path_steps / (double)(S[l].n + S[l].n_nonfinite);
         total += std::sqrt(V[l] * C[l]);
       }
       for (int l = lmin; l <= L; ++l) {
@@ -878,6 +913,22 @@ int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_par
                                   d_flags, (cudaStream_t)stream));
 }
 
+int mlmc_level_paths_steps_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                                 uint64_t seed, uint64_t path_offset, void* d_states,
+                                 int32_t* d_flags, int64_t* d_steps, void* stream) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (N && (!d_states || !d_flags || !d_steps)) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  if (!hm.adapt) return MLMC_EINVAL;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  return cuda_status(launch_adapt_paths(p->precision, integrator, hm, ls, N, path_offset, d_states,
+                                        d_flags, d_steps, (cudaStream_t)stream));
+}
+
 int mlmc_fp32_peak_probe(int iters, void* d_scratch, void* stream, double* flops_per_s) {
   if (iters < 1 || !d_scratch || !flops_per_s) return MLMC_EINVAL;
   DevInfo di;
@@ -912,6 +963,7 @@ int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_para
   HostModel hm;
   int rc = make_host_model(p, seed, &hm);
   if (rc) return rc;
+  if (hm.adapt) return MLMC_EINVAL;  // adaptive paths have no fixed time points
   LevelSpec ls;
   if ((rc = level_spec(hm, level, &ls))) return rc;
   if ((rc = check_stable(integrator, p, hm, ls))) return rc;
@@ -982,7 +1034,7 @@ static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int
       plan[k].item_paths = (uint32_t)item_paths;
       plan[k].n_items = (uint32_t)n_it;
       plan[k].item_base = (uint32_t)items;
-      plan[k].path_steps = reqs[k].count * steps_per_pair(ls);
+      plan[k].path_steps = fixed_steps(hm, ls, reqs[k].count);
       items += n_it;
     }
     if (items <= (uint64_t)kNoAllocItems) {

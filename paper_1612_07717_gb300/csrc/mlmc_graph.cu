@@ -228,6 +228,7 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
   HostModel hm;
   int rc = make_host_model(p, seed, &hm);
   if (rc) return rc;
+  if (hm.adapt) return MLMC_EINVAL;  // the device planner assumes fixed steps per pair
   for (int l = p->level_min; l <= p->L_max; ++l) {
     LevelSpec ls;
     if ((rc = level_spec(hm, l, &ls))) return rc;

@@ -15,10 +15,12 @@ constexpr int kMaxBlocksPerSM = 8;   // 2048 threads / kBlock
 
 // Partial sums of one thread block (or one work item), 128 bytes: for each
 // QoI sum Y, Y^2, P_f, P_f^2, P_c, P_c^2 (the indicator's sums are integer
-// counts held exactly in doubles), the finite pairs and the diverged pairs.
+// counts held exactly in doubles), the finite pairs, the diverged pairs and
+// the integrator steps counted on the device (adaptive timesteps; 0 when
+// the step count is fixed and known on the host).
 struct Partial {
   double s0[6], s1[6];
-  unsigned long long n, bad, pad[2];
+  unsigned long long n, bad, steps, pad;
 };
 static_assert(sizeof(Partial) == 128, "Partial layout");
 static_assert(sizeof(mlmc_level_result) == 128, "mlmc_level_result layout");
@@ -33,7 +35,11 @@ struct HostModel {
   int32_t qoi1_mode, smooth_r;        // smoothed interval QoI (Section 5.1)
   double qa, qb, delta;
   double pc[kMaxSmoothR + 2];         // p_r(s) = sum_k pc[k] s^k
+  int32_t adapt;                      // adaptive timesteps (Section 7.2)
+  double z_adapt, lam_a;              // X_adapt and lambda(X_adapt)
 };
+// Adaptive timesteps: time in ticks of (T / M0) 2^-kTickBits.
+constexpr int kTickBits = 40;
 // Coefficients of the smoothing polynomial p_r (Section 5.1); 0 or -1.
 int smooth_coefficients(int r, double* c);
 
@@ -89,6 +95,17 @@ cudaError_t launch_multilevel_table(int prec, int integ, const void* models, siz
 // Binned density of one level (k bins): per block 2k + 2 doubles.
 cudaError_t launch_pdf(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                        uint64_t offset, int k, double* partials, int grid, cudaStream_t st);
+// Adaptive timesteps (mlmc_adaptive.cu): the same launches for hm.adapt.
+// Level sums and multi-level partials count the integrator steps.
+cudaError_t launch_adapt_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                              uint64_t N, uint64_t offset, Partial* partials, int grid,
+                              cudaStream_t st);
+cudaError_t launch_adapt_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
+                                    int n_req, uint32_t n_items, Partial* partials,
+                                    unsigned int* counter, int grid, cudaStream_t st);
+cudaError_t launch_adapt_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
+                               uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
+                               int64_t* d_steps, cudaStream_t st);
 // Bytes of one device Model of precision prec, and its host image.
 size_t model_bytes(int prec);
 void model_image(int prec, const HostModel& hm, void* out);

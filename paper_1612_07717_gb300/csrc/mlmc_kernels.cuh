@@ -11,6 +11,7 @@
 //   k_paths       final states per pair (validation and per-particle output)
 //   k_trace       full trajectories (validation)
 #pragma once
+#include <cmath>
 #include <type_traits>
 
 #include "mlmc_device.cuh"
@@ -70,6 +71,10 @@ Model<R> make_model(const HostModel& h) {
   m.idelta = h.delta > 0.0 ? (R)(1.0 / h.delta) : R(0);
   for (int k = 0; k < 12; ++k) m.pc[k] = (R)h.pc[k];
   for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
+  m.za = (R)h.z_adapt;
+  m.lam_a = (R)h.lam_a;
+  m.sec = (R)std::ldexp(h.T / (double)h.M0, -kTickBits);
+  m.T_ticks = (uint64_t)h.M0 << kTickBits;
   return m;
 }
 
@@ -101,6 +106,7 @@ Level<R> make_level(const LevelSpec& s) {
 struct Acc {
   double y, y2, pf, pf2, pc, pc2;
   uint32_t n, bad, nf, nc, nd;
+  uint64_t steps;   // integrator steps (adaptive kernels; 0 otherwise)
 };
 
 __device__ __forceinline__ double (*q1_smem())[kBlock] {
@@ -118,6 +124,7 @@ __device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
 __device__ __forceinline__ void acc_zero(Acc& a, bool smooth) {
   a.y = a.y2 = a.pf = a.pf2 = a.pc = a.pc2 = 0.0;
   a.n = a.bad = a.nf = a.nc = a.nd = 0;
+  a.steps = 0;
   if (smooth) {
     double (*q)[kBlock] = q1_smem();
     for (int k = 0; k < 6; ++k) q[k][threadIdx.x] = 0.0;
@@ -169,7 +176,7 @@ __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, b
 __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, bool smooth,
                                                    Partial* __restrict__ out) {
   __shared__ double s_v[kBlock / 32][12];
-  __shared__ unsigned long long s_u[kBlock / 32][2];
+  __shared__ unsigned long long s_u[kBlock / 32][3];
   double v[12] = {a.y, a.y2, coupled ? a.pf : a.y, coupled ? a.pf2 : a.y2, a.pc, a.pc2};
   if (smooth) {
     double (*q)[kBlock] = q1_smem();
@@ -179,35 +186,36 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
     const double nf = (double)a.nf, nc = (double)a.nc, nd = (double)a.nd;
     v[6] = nf - nc; v[7] = nd; v[8] = nf; v[9] = nf; v[10] = nc; v[11] = nc;
   }
-  unsigned long long u[2] = {a.n, a.bad};
+  unsigned long long u[3] = {a.n, a.bad, a.steps};
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
-    s_u[warp][0] = u[0];
-    s_u[warp][1] = u[1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s[12], c[12];
     for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
-    unsigned long long t0 = 0, t1 = 0;
+    unsigned long long t[3] = {0, 0, 0};
     for (int w = 0; w < kBlock / 32; ++w) {
       for (int k = 0; k < 12; ++k) kahan_add(s[k], c[k], s_v[w][k]);
-      t0 += s_u[w][0];
-      t1 += s_u[w][1];
+      for (int k = 0; k < 3; ++k) t[k] += s_u[w][k];
     }
     for (int k = 0; k < 6; ++k) out->s0[k] = s[k] - c[k];
     for (int k = 0; k < 6; ++k) out->s1[k] = s[6 + k] - c[6 + k];
-    out->n = t0;
-    out->bad = t1;
+    out->n = t[0];
+    out->bad = t[1];
+    out->steps = t[2];
+    out->pad = 0;
   }
   __syncthreads();
 }

@@ -71,6 +71,7 @@ int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params
   HostModel hm;
   int rc = make_host_model(p, seed, &hm);
   if (rc) return rc;
+  if (hm.adapt) return MLMC_EINVAL;  // the density kernel takes uniform timesteps
   LevelSpec ls;
   if ((rc = level_spec(hm, level, &ls))) return rc;
   if ((rc = check_stable(integrator, p, hm, ls))) return rc;

@@ -250,6 +250,8 @@ int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t
   Query qq;
   int rc = make_host_model(p, s->seed, &qq.hm);
   if (rc) return rc;
+  if (qq.hm.adapt) return MLMC_EINVAL;  // batched queries take uniform timesteps
+
   for (int l = p->level_min; l <= p->L_max; ++l) {
     LevelSpec ls;
     if ((rc = level_spec(qq.hm, l, &ls))) return rc;

@@ -66,8 +66,11 @@ def adaptive_pair(p, integ, level, i, seed):
 
     def begin(P, t):
         c = coef(p, P["X"])
-        ratio = lam_a / c[1]
-        n = P["hmax"] if ratio >= 1 else max(1, math.floor(ratio * P["hmax"]))
+        H, e = p["H"], p["eps_reg_frac"] * p["H"]
+        n = P["hmax"]
+        if min(max(P["X"], e), H - e) < p["z_adapt"]:      # lambda(X_n) > lambda(X_adapt)
+            k = min(max(math.floor(1024 * (lam_a / c[1])), 1), 1024)
+            n = k * (P["hmax"] // 1024)
         n = min(n, T_ticks - t)
         P.update(c=c, n=n, end=t + n, ivals=[])
 
