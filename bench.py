@@ -27,21 +27,32 @@ N0 = 1e9
 # FP32 arithmetic per path-step of a coupled BAOAB level, counted from the
 # step formulas as the kernel evaluates them (FMA = 2; add, multiply,
 # reciprocal, reciprocal square root, exp2, log2, sin, cos = 1; compares,
-# selects, min/max = 0); the derivation is in the design doc.  Per coupled pair
-# of fine steps: 3 BAOAB steps of 53, the coarse coupling 9 and one
-# Box-Muller pair 13 -> 181 / 3 path-steps.
+# selects, min/max = 0).  A BAOAB step is 53 (B 5, A + fold 3, profile 11,
+# O-step factors 16, O 3, A + fold 3, drift terms 7, B 5); per coupled pair
+# of fine steps: 3 BAOAB steps, the coarse coupling 9 and one Box-Muller pair
+# 13 -> 181 / 3 path-steps.
 FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # DRAM bytes per launch of the path kernel from an ncu capture, valid only
-# for the kernel sources it was taken with (their SHA-1 over csrc/).
-TRAFFIC = {"csrc_sha1": "c9f44c209aa4e8434f8a41b1023398e68045cfc5", "bytes_per_launch": 0.855e6}
+# for the kernel sources it was taken with (their SHA-1, see kernel_sha1).
+TRAFFIC = {"kernel_sha1": "1206f2d34ec2fbbf91da74d73e44796ba9290067", "bytes_per_launch": 0.878e6}
+# The sources the persistent FP32 path kernels are compiled from.
+KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
+                  "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
+                  "paper_1612_07717_gb300/csrc/mlmc_device_x2.cuh",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels.cuh",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_inst.inc",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_f32.cu",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_f32_b3.cu",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_f32_b4.cu",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_f32_x2.cu",
+                  "paper_1612_07717_gb300/csrc/mlmc_kernels_f32_x2b3.cu")
 
 
-def csrc_sha1():
+def kernel_sha1():
     import hashlib
-    d = os.path.join(ROOT, "paper_1612_07717_gb300", "csrc")
     h = hashlib.sha1()
-    for name in sorted(os.listdir(d)):
-        with open(os.path.join(d, name), "rb") as f:
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 ORACLE_SAMPLE_SCALE = 2e-3
@@ -359,7 +370,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (TRAFFIC["bytes_per_launch"]
-                                     if TRAFFIC["csrc_sha1"] == csrc_sha1() else None),
+                                     if TRAFFIC["kernel_sha1"] == kernel_sha1() else None),
                          "peak_source": "measured FFMA probe" if peak_probe else
                          "derived SMs*128*2*clock at %.0f MHz" % sm_mhz,
                          "flops_per_path_step": FLOPS_PER_PATH_STEP},

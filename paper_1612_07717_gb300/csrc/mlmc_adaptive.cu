@@ -10,14 +10,31 @@
 namespace mlmc {
 namespace k_adapt {
 
+// The thread's pairs first + k, k = begin, begin + stride, ... < end, run
+// back to back: a finished pair is summed and the next one started at the
+// following round.  Every thread of the warp calls this (the loop condition
+// is a warp vote).
 template <int INTEG, typename R, bool COUPLED>
-__device__ __forceinline__ void adapt_add(const Model<R>& m, const Level<R>& lv, uint64_t i,
-                                          Acc& acc) {
-  APath<R> f, c;
-  bool bad;
-  run_pair_adapt<INTEG, R, COUPLED>(m, lv, i, f, c, bad);
-  acc_add<R, COUPLED>(acc, m, f.z, c.z, bad);
-  acc.steps += f.steps + (COUPLED ? c.steps : 0u);
+__device__ __forceinline__ void adapt_lane(const Model<R>& m, const Level<R>& lv, uint64_t first,
+                                           uint64_t begin, uint64_t end, uint64_t stride,
+                                           Acc& acc) {
+  uint64_t k = begin;
+  bool active = k < end;
+  APair<R> P;
+  if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
+  while (__any_sync(0xFFFFFFFFu, active)) {
+    if (active) {
+      apair_round<INTEG, R, COUPLED>(m, lv, P);
+      if (apair_done(P)) {
+        apair_finish<R, COUPLED>(P);
+        acc_add<R, COUPLED>(acc, m, P.f.z, P.c.z, P.bad);
+        acc.steps += P.f.steps + (COUPLED ? P.c.steps : 0u);
+        k += stride;
+        active = k < end;
+        if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
+      }
+    }
+  }
 }
 
 template <int INTEG, typename R, bool COUPLED>
@@ -25,14 +42,14 @@ __global__ void __launch_bounds__(kBlock) k_adapt_sums(const __grid_constant__ S
   Acc acc;
   acc_zero(acc, a.m.qoi1_mode != 0);
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < a.N; j += stride)
-    adapt_add<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, acc);
+  adapt_lane<INTEG, R, COUPLED>(a.m, a.lv, a.offset,
+                                (uint64_t)blockIdx.x * kBlock + threadIdx.x, a.N, stride, acc);
   block_reduce_store(acc, COUPLED, a.m.qoi1_mode != 0, a.partials + blockIdx.x);
 }
 
 // Persistent multi-level kernel: the work-item loop of k_multilevel.
 template <int INTEG, typename R>
-__global__ void __launch_bounds__(kBlock) k_adapt_multilevel(const __grid_constant__ MultiArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_adapt_multilevel(const __grid_constant__ MultiArgs<R> a) {
   __shared__ unsigned int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
@@ -49,10 +66,10 @@ __global__ void __launch_bounds__(kBlock) k_adapt_multilevel(const __grid_consta
     const Level<R> lv = rq.lv;
     Acc acc;
     acc_zero(acc, a.m.qoi1_mode != 0);
-    for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
-      if (lv.coupled) adapt_add<INTEG, R, true>(a.m, lv, rq.first + start + j, acc);
-      else adapt_add<INTEG, R, false>(a.m, lv, rq.first + start + j, acc);
-    }
+    if (lv.coupled)
+      adapt_lane<INTEG, R, true>(a.m, lv, rq.first + start, threadIdx.x, count, kBlock, acc);
+    else
+      adapt_lane<INTEG, R, false>(a.m, lv, rq.first + start, threadIdx.x, count, kBlock, acc);
     block_reduce_store(acc, lv.coupled != 0, a.m.qoi1_mode != 0, a.partials + it);
   }
 }

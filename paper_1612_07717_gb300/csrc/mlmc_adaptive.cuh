@@ -24,9 +24,13 @@
 // then uses S_i^(c) A (fine path: A) in place of sigma sqrt(h) xi (SE) or of
 // the O-step noise (GL).
 //
-// One loop iteration finishes exactly one step (the fine one first when
-// both end at the same tick), so every lane of a warp runs the same step
-// code whichever path it advances.
+// Work runs in rounds: a round draws one Philox block (four normals) for
+// every lane at once and iterates until the lane has used them; one
+// iteration finishes exactly one step (the fine one first when both end at
+// the same tick), so every lane of a warp runs the same step code whichever
+// path it advances.  A thread runs its pairs back to back (a finished pair
+// is replaced at the next round), so a lane with short pairs does not wait
+// for a warp-mate's long one; its pairs still enter its sums in index order.
 #pragma once
 #include "mlmc_device.cuh"
 
@@ -97,60 +101,106 @@ __device__ __forceinline__ void astep_finish(const Model<R>& m, APath<R>& p, R S
   p.steps += 1;
 }
 
+// State of one pair between rounds.
+template <typename R>
+struct APair {
+  APath<R> f, c;
+  uint64_t t;        // current tick (end of the last merged interval)
+  uint64_t cap;      // iteration bound of the pair
+  uint64_t it;       // iterations so far
+  uint32_t i_lo, w2; // counter words of the pair
+  uint32_t j;        // merged intervals consumed (a multiple of 4 between rounds)
+  bool bad;
+};
+
+// Start pair i of a level: the shared initial state and the first steps.
+template <typename R, bool COUPLED>
+__device__ __forceinline__ void apair_init(const Model<R>& m, const Level<R>& lv, uint64_t i,
+                                           APair<R>& P) {
+  P.i_lo = (uint32_t)i;
+  const uint32_t i_hi = (uint32_t)(i >> 32);
+  P.w2 = i_hi ^ lv.c2;
+  const int level = (int)(lv.c2 >> 24);
+  const uint64_t hf = 1ull << (kTickBits - level);
+  R z0, w0;
+  initial_state(m, lv, P.i_lo, i_hi, z0, w0);
+  P.f.z = z0; P.f.w = w0; P.f.S = R(1); P.f.steps = 0;
+  astep_begin(m, P.f, hf, 0);
+  P.c = P.f;
+  if (COUPLED) astep_begin(m, P.c, hf << 1, 0);
+  else P.c.t_end = kNoStep;
+  // lambda(X_adapt) >= lambda_max / 1024 bounds the steps of a pair by
+  // 1024 (M + M/2) (plus the rounding of each step to whole ticks)
+  P.cap = 2048ull * (uint64_t)lv.M + 64;
+  P.it = 0;
+  P.t = 0;
+  P.j = 0;
+  P.bad = false;
+}
+
+template <typename R>
+__device__ __forceinline__ bool apair_done(const APair<R>& P) {
+  return P.bad || (P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end) == kNoStep;
+}
+
+// One round: the four normals of Philox block j / 4, then iterations until
+// they are used or the pair is done.  Each iteration adds the merged interval
+// [t, tn] (if not empty) to both paths and finishes exactly one step (the
+// fine one first when both end at tn), so every lane runs the same step
+// code whichever path it advances.
+template <int INTEG, typename R, bool COUPLED>
+__device__ __forceinline__ void apair_round(const Model<R>& m, const Level<R>& lv, APair<R>& P) {
+  const int level = (int)(lv.c2 >> 24);
+  const uint64_t hf = 1ull << (kTickBits - level), hc = hf << 1;
+  const uint4 x = philox10(m.rk0, m.rk1, P.j >> 2, P.i_lo, P.w2, m.stream_id);
+  R x0, x1, x2, x3;
+  box_muller(x.x, x.y, x0, x1);
+  box_muller(x.z, x.w, x2, x3);
+  uint32_t q = 0;
+  while (q < 4u) {
+    const uint64_t tn = P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end;
+    if (tn == kNoStep) break;
+    if (P.it >= P.cap) { P.bad = true; break; }
+    P.it += 1;
+    if (tn > P.t) {                      // the merged interval [t, tn] with xi_j
+      const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
+      const R d = (R)(tn - P.t) * m.sec;
+      accumulate<INTEG>(P.f, d, xi, R(1));
+      if (COUPLED) accumulate<INTEG>(P.c, d, xi, m.coupling ? R(1) : P.f.S);  // S_j^(f)
+      ++q;
+      P.t = tn;
+    }
+    const bool fine = P.f.t_end == P.t;
+    APath<R> p = fine ? P.f : P.c;
+    const R Sx = (fine || m.coupling) ? R(1) : p.S;                          // S_i^(c)
+    astep_finish<INTEG>(m, p, Sx, P.bad);
+    if (p.t_end == m.T_ticks) p.t_end = kNoStep;
+    else astep_begin(m, p, fine ? hf : hc, P.t);
+    if (fine) P.f = p;
+    else P.c = p;
+    if (P.bad) break;
+  }
+  P.j += 4;
+}
+
+template <typename R, bool COUPLED>
+__device__ __forceinline__ void apair_finish(APair<R>& P) {
+  P.bad |= !(isfinite(P.f.z) && isfinite(P.f.w));
+  if (COUPLED) P.bad |= !(isfinite(P.c.z) && isfinite(P.c.w));
+}
+
 // One path pair of a level with adaptive timesteps (fine only when not
 // COUPLED).  `bad` marks a diverged pair (or one past the step bound).
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void run_pair_adapt(const Model<R>& m, const Level<R>& lv, uint64_t i,
                                                APath<R>& f, APath<R>& c, bool& bad) {
-  const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
-  const uint32_t w2 = i_hi ^ lv.c2;
-  const int level = (int)(lv.c2 >> 24);
-  const uint64_t hf = 1ull << (kTickBits - level), hc = hf << 1;
-  R z0, w0;
-  initial_state(m, lv, i_lo, i_hi, z0, w0);
-  f.z = z0; f.w = w0; f.S = R(1); f.steps = 0;
-  bad = false;
-  astep_begin(m, f, hf, 0);
-  c = f;
-  if (COUPLED) astep_begin(m, c, hc, 0);
-  else c.t_end = kNoStep;
-  // lambda(X_adapt) >= lambda_max / 1024 bounds the steps of a pair by
-  // 1024 (M + M/2) (plus the rounding of each step to whole ticks)
-  const uint64_t cap = 2048ull * (uint64_t)lv.M + 64;
-  uint64_t t = 0;
-  uint32_t j = 0, blk = 0xFFFFFFFFu;
-  R x0 = R(0), x1 = R(0), x2 = R(0), x3 = R(0);
-  for (uint64_t it = 0;; ++it) {
-    const uint64_t tn = f.t_end < c.t_end ? f.t_end : c.t_end;
-    if (tn == kNoStep) break;
-    if (it >= cap) { bad = true; break; }
-    if (tn > t) {                       // the merged interval [t, tn] with xi_j
-      if ((j >> 2) != blk) {
-        blk = j >> 2;
-        const uint4 x = philox10(m.rk0, m.rk1, blk, i_lo, w2, m.stream_id);
-        box_muller(x.x, x.y, x0, x1);
-        box_muller(x.z, x.w, x2, x3);
-      }
-      const uint32_t q = j & 3u;
-      const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
-      const R d = (R)(tn - t) * m.sec;
-      accumulate<INTEG>(f, d, xi, R(1));
-      if (COUPLED) accumulate<INTEG>(c, d, xi, m.coupling ? R(1) : f.S);  // S_j^(f)
-      ++j;
-      t = tn;
-    }
-    const bool fine = f.t_end == t;
-    APath<R> p = fine ? f : c;
-    const R Sx = (fine || m.coupling) ? R(1) : p.S;                        // S_i^(c)
-    astep_finish<INTEG>(m, p, Sx, bad);
-    if (p.t_end == m.T_ticks) p.t_end = kNoStep;
-    else astep_begin(m, p, fine ? hf : hc, t);
-    if (fine) f = p;
-    else c = p;
-    if (bad) break;
-  }
-  bad |= !(isfinite(f.z) && isfinite(f.w));
-  if (COUPLED) bad |= !(isfinite(c.z) && isfinite(c.w));
+  APair<R> P;
+  apair_init<R, COUPLED>(m, lv, i, P);
+  while (!apair_done(P)) apair_round<INTEG, R, COUPLED>(m, lv, P);
+  apair_finish<R, COUPLED>(P);
+  f = P.f;
+  c = P.c;
+  bad = P.bad;
 }
 
 }  // namespace mlmc

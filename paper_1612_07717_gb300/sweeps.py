@@ -1,0 +1,79 @@
+"""Cost against tolerance in the paper's scenario (Section 6.1, Fig.
+CostRatesPosition; Section 7.3 for adaptive timesteps).
+
+For each RMSE tolerance eps on E[X_T] and each integrator:
+
+* MLMC: the adaptive estimator (``estimate_graph``, or the host-driven
+  ``estimate`` for adaptive timesteps); cost = integrator steps taken;
+* StMC: plain Monte Carlo at the finest timestep the MLMC hierarchy needed
+  for the same eps (so both have the same bias), N = 2 Var / eps^2 paths
+  (``stmc_estimate``).
+
+Both use FP32 paths with FP64 sums, so the step counts compare the two
+algorithms on equal terms.
+
+Run on a GPU: ``python -m paper_1612_07717_gb300.sweeps [out.json]``.
+"""
+import json
+import math
+import sys
+import time
+
+from . import (BAOAB, FP32, GL, SE, Workspace, estimate, estimate_graph, make_params,
+               stmc_estimate)
+from . import workloads as W
+
+NAMES = {SE: "SE", GL: "GL", BAOAB: "BAOAB"}
+EPS = (1e-3, 5e-4, 2e-4, 1e-4, 5e-5)
+
+
+def mlmc_cost(eps, integ, seed=1, z_adapt=0.0, n_init=4000, L_max=12, precision=FP32):
+    d = dict(W.PAPER, n_init=n_init, L_max=L_max, z_adapt=z_adapt)
+    p = make_params(d, precision=precision)
+    ws = Workspace(p)
+    run = estimate if z_adapt > 0 else estimate_graph
+    t = time.perf_counter()
+    r = run(eps, integ, p, seed, workspace=ws)
+    dt = time.perf_counter() - t
+    return dict(L=r["L"], converged=r["converged"], estimate=r["estimate"][0],
+                rmse_stat=math.sqrt(r["est_variance"][0]), path_steps=r["total_path_steps"],
+                seconds=dt, N=r["N"])
+
+
+def stmc_cost(eps, integ, level, seed=2, n_pilot=4000, precision=FP32):
+    p = make_params(dict(W.PAPER, level_min=level), precision=precision)
+    t = time.perf_counter()
+    s = stmc_estimate(eps, level, integ, p, seed, n_pilot=n_pilot, workspace=Workspace(p))
+    dt = time.perf_counter() - t
+    return dict(level=level, h=W.PAPER["T"] / (W.PAPER["M0"] << level), N=s["N"][0],
+                estimate=s["estimate"][0], path_steps=s["total_path_steps"], seconds=dt)
+
+
+def paper_cost_sweep(eps_list=EPS, integrators=(SE, GL, BAOAB)):
+    out = []
+    for integ in integrators:
+        for eps in eps_list:
+            m = mlmc_cost(eps, integ)
+            s = stmc_cost(eps, integ, m["L"])
+            out.append(dict(integrator=NAMES[integ], eps=eps, mlmc=m, stmc=s))
+    return out
+
+
+def adaptive_cost_sweep(eps_list=EPS, integrators=(SE, GL), x_adapt=0.05):
+    out = []
+    for integ in integrators:
+        for eps in eps_list:
+            out.append(dict(integrator=NAMES[integ], eps=eps,
+                            uniform=mlmc_cost(eps, integ),
+                            adaptive=mlmc_cost(eps, integ, z_adapt=x_adapt)))
+    return out
+
+
+if __name__ == "__main__":
+    res = dict(scenario="paper (H = 1, u* = 0.2, T = 1, X0 = 0.05, U0 = 0.1, eps_reg = 0.01, M0 = 40)",
+               cost=paper_cost_sweep(), adaptive=adaptive_cost_sweep())
+    text = json.dumps(res, indent=1)
+    if len(sys.argv) > 1:
+        with open(sys.argv[1], "w") as f:
+            f.write(text)
+    print(text)
