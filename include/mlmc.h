@@ -101,14 +101,16 @@ typedef struct mlmc_params {
   double smooth_delta;  /* smoothing width delta [m], > 0 when smoothing is used */
   double z_adapt;       /* 0: uniform timesteps.  > 0: adaptive, non-nested
                            timesteps with reference height X_adapt = z_adapt [m]
-                           (Section 7.2): h_n = min(h, lambda(X_adapt) /
-                           lambda(X_n) h) in whole ticks of (T / M0) 2^-40, the
-                           coupled pair driven on the merged time grid.  SE and
-                           GL only; needs 0 < z_adapt <= H, M0 <= 2^22 and
-                           lambda(X_adapt) >= lambda_max / 1024.  Supported by
-                           the level-sums, multi-level, estimate and path
-                           entry points; the graph, server and density entry
-                           points return MLMC_EINVAL for it.                  */
+                           (Section 7.2): below X_adapt a step is shortened to
+                           floor(1024 lambda(X_adapt) / lambda(X_n)) / 1024 of h
+                           (the paper's min(h, lambda(X_adapt) / lambda(X_n) h)
+                           rounded down to a 1024th of h), the coupled pair is
+                           driven on the merged time grid.  SE and GL only;
+                           needs 0 < z_adapt <= H, M_l <= 2^21 on the levels
+                           used, and lambda(X_adapt) >= lambda_max / 1024.
+                           Supported by the level-sums, multi-level, estimate
+                           and path entry points; the graph, server, density
+                           and trace entry points return MLMC_EINVAL for it. */
 } mlmc_params;
 
 /* Fill *p with the 600 m neutral boundary-layer scenario: u* = 0.2, f = 1e-4,

@@ -24,11 +24,11 @@ __device__ __forceinline__ void adapt_lane(const Model<R>& m, const Level<R>& lv
   if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
   while (__any_sync(0xFFFFFFFFu, active)) {
     if (active) {
-      apair_round<INTEG, R, COUPLED>(m, lv, P);
+      apair_round<INTEG, R, COUPLED>(m, P);
       if (apair_done(P)) {
         apair_finish<R, COUPLED>(P);
         acc_add<R, COUPLED>(acc, m, P.f.z, P.c.z, P.bad);
-        acc.steps += P.f.steps + (COUPLED ? P.c.steps : 0u);
+        acc.steps += P.nf + P.nc;
         k += stride;
         active = k < end;
         if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
@@ -88,17 +88,16 @@ template <int INTEG, typename R, bool COUPLED>
 __global__ void __launch_bounds__(kBlock) k_adapt_paths(const __grid_constant__ AdaptPathsArgs<R> a) {
   const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (j >= a.N) return;
-  APath<R> f, c;
-  bool bad;
-  run_pair_adapt<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad);
+  APair<R> P;
+  run_pair_adapt<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, P);
   R* o = a.states + 4 * j;
-  o[0] = f.z; o[1] = f.w;
-  o[2] = COUPLED ? c.z : R(0);
-  o[3] = COUPLED ? c.w : R(0);
-  a.flags[j] = bad ? 1 : 0;
+  o[0] = P.f.z; o[1] = P.f.w;
+  o[2] = COUPLED ? P.c.z : R(0);
+  o[3] = COUPLED ? P.c.w : R(0);
+  a.flags[j] = P.bad ? 1 : 0;
   if (a.steps) {
-    a.steps[2 * j] = f.steps;
-    a.steps[2 * j + 1] = COUPLED ? c.steps : 0;
+    a.steps[2 * j] = P.nf;
+    a.steps[2 * j + 1] = P.nc;
   }
 }
 

@@ -6,10 +6,10 @@
 // lambda decreases with height, so the ratio is below 1 exactly when the
 // clamped X_n lies below X_adapt; the step is then floor(1024 ratio) / 1024
 // of h (at least 1/1024 by the parameter check): the same rule on every
-// level and never longer than the paper's step.  Time runs in integer ticks
-// of (T / M0) 2^-40, so h_l = 2^(40 - l) ticks, every step is a whole number
-// of ticks, the last step of a path ends exactly at T, and fine and coarse
-// time points of a pair are compared exactly.
+// level and never longer than the paper's step.  Time runs in integer units
+// of h_l / 1024 (32 bits): a fine step is at most 1024 units, a coarse one
+// 2048, T is 1024 M_l, the last step of a path ends exactly at T, and fine
+// and coarse time points of a pair are compared exactly.
 //
 // Coupling on the merged grid: interval j between consecutive fine or
 // coarse time points carries the normal xi_j (element j mod 4 of Philox
@@ -36,7 +36,7 @@
 
 namespace mlmc {
 
-constexpr uint64_t kNoStep = ~0ull;  // t_end of a path that has reached T
+constexpr uint32_t kNoStep = 0xFFFFFFFFu;  // t_end of a path that has reached T
 
 template <typename R>
 struct APath {
@@ -45,29 +45,29 @@ struct APath {
   R h;                // length of the current step [s]
   R A;                // sigma times the noise increment accumulated so far
   R E;                // GL: exp(-lambda x the part of the step accumulated so far)
-  uint64_t t_end;     // tick at which the current step ends
-  uint32_t steps;     // steps taken
+  uint32_t t_end;     // unit at which the current step ends
 };
 
 __device__ __forceinline__ float adiv(float a, float b) { return a * ptx_rcp(b); }
 __device__ __forceinline__ double adiv(double a, double b) { return a / b; }
 
-// Start a step of a path at tick t: the profile at X_n, the step rule, the
-// cap at T.  hmax: h of the path in ticks.
+// Start a step of a path at unit t: the profile at X_n, the step rule, the
+// cap at T.  scale: 1 for the fine path, 2 for the coarse one (its h is 2048
+// units); usec: seconds per unit.
 template <typename R>
-__device__ __forceinline__ void astep_begin(const Model<R>& m, APath<R>& p, uint64_t hmax,
-                                            uint64_t t) {
+__device__ __forceinline__ void astep_begin(const Model<R>& m, APath<R>& p, uint32_t scale,
+                                            uint32_t t, uint32_t T_units, R usec) {
   profile(m, p.z, p.su, p.lam, p.g0, p.g1);
   const R zc = fmin_(fmax_(p.z, m.eps), m.Hme);
-  uint64_t n = hmax;
+  uint32_t k = 1024u;
   if (zc < m.za) {
-    uint32_t k = (uint32_t)(R(1024) * adiv(m.lam_a, p.lam));  // floor of a positive value
+    k = (uint32_t)(R(1024) * adiv(m.lam_a, p.lam));  // floor of a positive value
     k = k < 1u ? 1u : (k > 1024u ? 1024u : k);
-    n = (uint64_t)k * (hmax >> 10);
   }
-  const uint64_t left = m.T_ticks - t;
+  uint32_t n = k * scale;
+  const uint32_t left = T_units - t;
   n = n < left ? n : left;
-  p.h = (R)n * m.sec;
+  p.h = (R)n * usec;
   p.t_end = t + n;
   p.A = R(0);
   p.E = R(1);
@@ -98,18 +98,20 @@ __device__ __forceinline__ void astep_finish(const Model<R>& m, APath<R>& p, R S
   }
   p.z = fma(p.w, p.h, p.z);                           // A
   reflect_exact(m, p.z, p.w, p.S, bad);
-  p.steps += 1;
 }
 
 // State of one pair between rounds.
 template <typename R>
 struct APair {
   APath<R> f, c;
-  uint64_t t;        // current tick (end of the last merged interval)
-  uint64_t cap;      // iteration bound of the pair
-  uint64_t it;       // iterations so far
+  uint32_t t;        // current unit (end of the last merged interval)
+  uint32_t T_units;  // T in units of h_l / 1024
+  uint32_t cap;      // iteration bound of the pair
+  uint32_t it;       // iterations so far: one per step of either path
   uint32_t i_lo, w2; // counter words of the pair
   uint32_t j;        // merged intervals consumed (a multiple of 4 between rounds)
+  uint32_t nf, nc;   // steps taken by the fine and the coarse path
+  R usec;            // seconds per unit
   bool bad;
 };
 
@@ -120,19 +122,20 @@ __device__ __forceinline__ void apair_init(const Model<R>& m, const Level<R>& lv
   P.i_lo = (uint32_t)i;
   const uint32_t i_hi = (uint32_t)(i >> 32);
   P.w2 = i_hi ^ lv.c2;
-  const int level = (int)(lv.c2 >> 24);
-  const uint64_t hf = 1ull << (kTickBits - level);
+  P.T_units = (uint32_t)lv.M << 10;
+  P.usec = lv.h * R(0.0009765625);
   R z0, w0;
   initial_state(m, lv, P.i_lo, i_hi, z0, w0);
-  P.f.z = z0; P.f.w = w0; P.f.S = R(1); P.f.steps = 0;
-  astep_begin(m, P.f, hf, 0);
+  P.f.z = z0; P.f.w = w0; P.f.S = R(1);
+  astep_begin(m, P.f, 1u, 0u, P.T_units, P.usec);
   P.c = P.f;
-  if (COUPLED) astep_begin(m, P.c, hf << 1, 0);
+  if (COUPLED) astep_begin(m, P.c, 2u, 0u, P.T_units, P.usec);
   else P.c.t_end = kNoStep;
-  // lambda(X_adapt) >= lambda_max / 1024 bounds the steps of a pair by
-  // 1024 (M + M/2) (plus the rounding of each step to whole ticks)
-  P.cap = 2048ull * (uint64_t)lv.M + 64;
+  // every step is at least one unit: at most T_units steps per path
+  P.cap = 2u * P.T_units + 64u;
   P.it = 0;
+  P.nf = 0;
+  P.nc = 0;
   P.t = 0;
   P.j = 0;
   P.bad = false;
@@ -149,33 +152,33 @@ __device__ __forceinline__ bool apair_done(const APair<R>& P) {
 // fine one first when both end at tn), so every lane runs the same step
 // code whichever path it advances.
 template <int INTEG, typename R, bool COUPLED>
-__device__ __forceinline__ void apair_round(const Model<R>& m, const Level<R>& lv, APair<R>& P) {
-  const int level = (int)(lv.c2 >> 24);
-  const uint64_t hf = 1ull << (kTickBits - level), hc = hf << 1;
+__device__ __forceinline__ void apair_round(const Model<R>& m, APair<R>& P) {
   const uint4 x = philox10(m.rk0, m.rk1, P.j >> 2, P.i_lo, P.w2, m.stream_id);
   R x0, x1, x2, x3;
   box_muller(x.x, x.y, x0, x1);
   box_muller(x.z, x.w, x2, x3);
   uint32_t q = 0;
   while (q < 4u) {
-    const uint64_t tn = P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end;
+    const uint32_t tn = P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end;
     if (tn == kNoStep) break;
     if (P.it >= P.cap) { P.bad = true; break; }
     P.it += 1;
     if (tn > P.t) {                      // the merged interval [t, tn] with xi_j
       const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
-      const R d = (R)(tn - P.t) * m.sec;
+      const R d = (R)(tn - P.t) * P.usec;
       accumulate<INTEG>(P.f, d, xi, R(1));
       if (COUPLED) accumulate<INTEG>(P.c, d, xi, m.coupling ? R(1) : P.f.S);  // S_j^(f)
       ++q;
       P.t = tn;
     }
     const bool fine = P.f.t_end == P.t;
+    P.nf += fine ? 1u : 0u;
+    P.nc += fine ? 0u : 1u;
     APath<R> p = fine ? P.f : P.c;
     const R Sx = (fine || m.coupling) ? R(1) : p.S;                          // S_i^(c)
     astep_finish<INTEG>(m, p, Sx, P.bad);
-    if (p.t_end == m.T_ticks) p.t_end = kNoStep;
-    else astep_begin(m, p, fine ? hf : hc, P.t);
+    if (p.t_end == P.T_units) p.t_end = kNoStep;
+    else astep_begin(m, p, fine ? 1u : 2u, P.t, P.T_units, P.usec);
     if (fine) P.f = p;
     else P.c = p;
     if (P.bad) break;
@@ -190,17 +193,13 @@ __device__ __forceinline__ void apair_finish(APair<R>& P) {
 }
 
 // One path pair of a level with adaptive timesteps (fine only when not
-// COUPLED).  `bad` marks a diverged pair (or one past the step bound).
+// COUPLED).  P.bad marks a diverged pair (or one past the step bound).
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void run_pair_adapt(const Model<R>& m, const Level<R>& lv, uint64_t i,
-                                               APath<R>& f, APath<R>& c, bool& bad) {
-  APair<R> P;
+                                               APair<R>& P) {
   apair_init<R, COUPLED>(m, lv, i, P);
-  while (!apair_done(P)) apair_round<INTEG, R, COUPLED>(m, lv, P);
+  while (!apair_done(P)) apair_round<INTEG, R, COUPLED>(m, P);
   apair_finish<R, COUPLED>(P);
-  f = P.f;
-  c = P.c;
-  bad = P.bad;
 }
 
 }  // namespace mlmc

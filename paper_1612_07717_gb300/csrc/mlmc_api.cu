@@ -472,7 +472,7 @@ int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
 // lambda(X_adapt) in place of lambda_max.
 int check_stable(int integ, const mlmc_params* p, const HostModel& hm, const LevelSpec& ls) {
   if (hm.adapt && integ == MLMC_BAOAB) return MLMC_EINVAL;
-  if (hm.adapt && ls.level > kTickBits - 10) return MLMC_EINVAL;
+  if (hm.adapt && ls.M > kAdaptMaxM) return MLMC_EINVAL;
   if (integ != MLMC_SE || p->allow_unstable) return MLMC_OK;
   const double hmax = ls.coupled ? 2.0 * ls.h : ls.h;  // the coarse path steps 2h
   const double lam = hm.adapt ? hm.lam_a : lambda_max(hm);

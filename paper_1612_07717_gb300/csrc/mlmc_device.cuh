@@ -42,8 +42,6 @@ struct Model {
   uint32_t rk0[10], rk1[10];  // Philox round keys of the seed
   // adaptive timesteps (Section 7.2)
   R za, lam_a;          // X_adapt and lambda(X_adapt)
-  R sec;                // seconds per tick: (T / M0) 2^-40
-  uint64_t T_ticks;     // T in ticks: M0 2^40
 };
 
 // Per-level constants.

@@ -38,8 +38,9 @@ struct HostModel {
   int32_t adapt;                      // adaptive timesteps (Section 7.2)
   double z_adapt, lam_a;              // X_adapt and lambda(X_adapt)
 };
-// Adaptive timesteps: time in ticks of (T / M0) 2^-kTickBits.
-constexpr int kTickBits = 40;
+// Adaptive timesteps count time in units of h_l / 1024 of the level: T is
+// 1024 M_l units, which must stay below 2^31.
+constexpr int64_t kAdaptMaxM = (int64_t)1 << 21;
 // Coefficients of the smoothing polynomial p_r (Section 5.1); 0 or -1.
 int smooth_coefficients(int r, double* c);
 

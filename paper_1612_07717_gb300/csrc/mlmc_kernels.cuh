@@ -11,7 +11,6 @@
 //   k_paths       final states per pair (validation and per-particle output)
 //   k_trace       full trajectories (validation)
 #pragma once
-#include <cmath>
 #include <type_traits>
 
 #include "mlmc_device.cuh"
@@ -73,8 +72,6 @@ Model<R> make_model(const HostModel& h) {
   for (int r = 0; r < 10; ++r) { m.rk0[r] = h.rk0[r]; m.rk1[r] = h.rk1[r]; }
   m.za = (R)h.z_adapt;
   m.lam_a = (R)h.lam_a;
-  m.sec = (R)std::ldexp(h.T / (double)h.M0, -kTickBits);
-  m.T_ticks = (uint64_t)h.M0 << kTickBits;
   return m;
 }
 
