@@ -34,7 +34,7 @@ N0 = 1e9
 FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # DRAM bytes per launch of the path kernel from an ncu capture, valid only
 # for the kernel sources it was taken with (their SHA-1, see kernel_sha1).
-TRAFFIC = {"kernel_sha1": "1206f2d34ec2fbbf91da74d73e44796ba9290067", "bytes_per_launch": 0.878e6}
+TRAFFIC = {"kernel_sha1": "c3016a711852b3672a99e63814110109403ed03f", "bytes_per_launch": 0.912e6}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
