@@ -56,7 +56,9 @@ typedef enum {
   MLMC_EUNSTABLE = -6,   /* symplectic Euler requested with h lambda_max >= 2   */
   MLMC_ENOTCONV = -7,    /* adaptive driver reached L_max before its bias test
                             passed; the estimate is still returned              */
-  MLMC_ENODEV = -8       /* no CUDA device or unsupported architecture          */
+  MLMC_ENODEV = -8,      /* no CUDA device or unsupported architecture          */
+  MLMC_ECOMM = -9        /* the all-reduce hook failed, or another rank of a
+                            sharded estimate reported an error                  */
 } mlmc_status;
 
 typedef enum { MLMC_SE = 0, MLMC_GL = 1, MLMC_BAOAB = 2 } mlmc_integrator;
@@ -254,6 +256,25 @@ int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req, int 
  * Host-driven loop of mlmc_level_sums calls on `stream`. */
 int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed,
                   void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
+
+/* mlmc_estimate sharded over `world` ranks (one per GPU; the paper has no
+ * counterpart: paths are independent and keyed by global index, so any
+ * split gives the same samples).  In every pass rank `rank` integrates its
+ * contiguous slice of each level's new path range [N_done, N_done + dN) on
+ * its own device, and calls reduce(buf, n, ctx) once, which must replace the
+ * n doubles of buf by their element-wise sum over all ranks (an all-reduce,
+ * called by every rank in the same order) and return 0.  buf holds per level
+ * the pair count, the diverged count, the steps, the twelve FP64 sums and,
+ * in the last slot, an error flag: a rank whose launch failed still joins
+ * the reduction, and then every rank returns its error (MLMC_ECOMM on the
+ * others).  All ranks then apply the same N_l and bias-test decisions, so
+ * they return the same result, equal to mlmc_estimate's up to the FP64
+ * rounding of the cross-rank sum.  world = 1 needs no hook.  A hook that
+ * returns non-zero gives MLMC_ECOMM. */
+typedef int (*mlmc_allreduce_fn)(double* buf, int n, void* ctx);
+int mlmc_estimate_sharded(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                          int rank, int world, mlmc_allreduce_fn reduce, void* ctx,
+                          void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
 
 /* The same adaptive estimate with the whole loop on the device, as one CUDA
  * graph: an init kernel, then a conditional while-node whose body is the

@@ -20,8 +20,11 @@ SE, GL, BAOAB = 0, 1, 2
 FP32, FP64 = 0, 1
 MAX_LEVELS = 32
 
-OK, EINVAL, EWORKSPACE, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTCONV, ENODEV = (
-    0, -1, -2, -3, -4, -5, -6, -7, -8)
+OK, EINVAL, EWORKSPACE, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTCONV, ENODEV, ECOMM = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
+
+# reduce hook of mlmc_estimate_sharded: int (*)(double* buf, int n, void* ctx)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmlmc.so")
@@ -96,6 +99,9 @@ def lib():
                                            u64, vp, C.c_size_t, vp, C.POINTER(LevelResult)]
         L.mlmc_estimate.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t, vp,
                                     C.POINTER(Result)]
+        L.mlmc_estimate_sharded.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, i32,
+                                            ALLREDUCE_FN, vp, vp, C.c_size_t, vp,
+                                            C.POINTER(Result)]
         L.mlmc_graph_create.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
                                         C.POINTER(vp)]
         L.mlmc_graph_launch.argtypes = [vp, vp]
@@ -276,6 +282,49 @@ def estimate(eps, integrator, params, seed, workspace=None, stream=None):
     rc = lib().mlmc_estimate(eps, integrator, C.byref(params), seed, *ws.args(),
                              _stream_handle(stream), C.byref(r))
     _check(rc, "mlmc_estimate", allow=(ENONFINITE, ENOTCONV))
+    out = _result(r, params.level_min)
+    out["status"] = rc
+    return out
+
+
+def torch_allreduce(group=None):
+    """A reduce hook for estimate_sharded over a torch.distributed group:
+    the buffer goes through a float64 tensor on the group's device (CPU for
+    gloo, the current CUDA device for nccl) and an all-reduce SUM."""
+    import torch
+    import torch.distributed as dist
+
+    def reduce(values):
+        dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        t = torch.tensor(values, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t.cpu().tolist()
+    return reduce
+
+
+def estimate_sharded(eps, integrator, params, seed, rank, world, reduce, workspace=None,
+                     stream=None):
+    """mlmc_estimate_sharded: this rank's share of every level, the sums
+    combined by reduce(list of floats) -> list of their sums over ranks."""
+    ws = workspace or Workspace(params)
+    failed = []
+
+    def hook(buf, n, ctx):
+        try:
+            vals = reduce([buf[k] for k in range(n)])
+            for k in range(n):
+                buf[k] = float(vals[k])
+            return 0
+        except Exception as e:          # reported to the library as a failed reduction
+            failed.append(e)
+            return 1
+    cb = ALLREDUCE_FN(hook)
+    r = Result()
+    rc = lib().mlmc_estimate_sharded(eps, integrator, C.byref(params), seed, rank, world, cb,
+                                     None, *ws.args(), _stream_handle(stream), C.byref(r))
+    if failed:
+        raise MLMCError(rc, "mlmc_estimate_sharded (reduce hook: %r)" % failed[0])
+    _check(rc, "mlmc_estimate_sharded", allow=(ENONFINITE, ENOTCONV))
     out = _result(r, params.level_min)
     out["status"] = rc
     return out

@@ -73,15 +73,19 @@ __device__ __forceinline__ void astep_begin(const Model<R>& m, APath<R>& p, uint
   p.E = R(1);
 }
 
-// Add an interval of d > 0 seconds with normal xi and parity weight wgt.
+// Add an interval of d seconds with normal xi and parity weight wgt.  An
+// empty interval (d = 0, wgt = 0) leaves the path unchanged: e = 2^0 = 1 and
+// the square root's argument is kept positive (the floor is far below any
+// real interval's 2 lambda d or 1 - e^2), so its product with wgt = 0 is 0.
 template <int INTEG, typename R>
 __device__ __forceinline__ void accumulate(APath<R>& p, R d, R xi, R wgt) {
+  const R tiny = R(1e-30);
   if (INTEG == kSE) {
-    p.A = fma(wgt * (p.su * sqrt_((R(2) * p.lam) * d)), xi, p.A);
+    p.A = fma(wgt * (p.su * sqrt_(fmax_((R(2) * p.lam) * d, tiny))), xi, p.A);
   } else {
     R e, om;
     exp_pair(p.lam * (d * R(1.4426950408889634074)), e, om);
-    p.A = fma(wgt * (p.su * sqrt_(om)), xi, p.A * e);
+    p.A = fma(wgt * (p.su * sqrt_(fmax_(om, tiny))), xi, p.A * e);
     p.E *= e;
   }
 }
@@ -163,14 +167,16 @@ __device__ __forceinline__ void apair_round(const Model<R>& m, APair<R>& P) {
     if (tn == kNoStep) break;
     if (P.it >= P.cap) { P.bad = true; break; }
     P.it += 1;
-    if (tn > P.t) {                      // the merged interval [t, tn] with xi_j
-      const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
-      const R d = (R)(tn - P.t) * P.usec;
-      accumulate<INTEG>(P.f, d, xi, R(1));
-      if (COUPLED) accumulate<INTEG>(P.c, d, xi, m.coupling ? R(1) : P.f.S);  // S_j^(f)
-      ++q;
-      P.t = tn;
-    }
+    // the merged interval [t, tn] with xi_j; empty (and a no-op) when the
+    // step just finished ends at the same unit as the other path's
+    const bool iv = tn > P.t;
+    const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
+    const R d = (R)(tn - P.t) * P.usec;
+    accumulate<INTEG>(P.f, d, xi, iv ? R(1) : R(0));
+    if (COUPLED)
+      accumulate<INTEG>(P.c, d, xi, iv ? (m.coupling ? R(1) : P.f.S) : R(0));  // S_j^(f)
+    q += iv ? 1u : 0u;
+    P.t = tn;
     const bool fine = P.f.t_end == P.t;
     P.nf += fine ? 1u : 0u;
     P.nc += fine ? 0u : 1u;

@@ -524,6 +524,7 @@ const char* mlmc_strerror(int code) {
     case MLMC_EUNSTABLE: return "symplectic Euler is unstable at this timestep (h lambda_max >= 2)";
     case MLMC_ENOTCONV: return "adaptive driver reached L_max before its bias test passed";
     case MLMC_ENODEV: return "no usable CUDA device";
+    case MLMC_ECOMM: return "the all-reduce hook failed or another rank reported an error";
     default: return "unknown status";
   }
 }
@@ -768,12 +769,30 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
 //   sqrt(V_l / C_l) sum_k sqrt(V_k C_k));  4. run the extra samples;
 //   5. if L >= level_min + 2 stop when max(|Yhat_{L-1}| / 2, |Yhat_L|) <
 //   eps / sqrt(2);  6. else L += 1 (up to L_max) and go to 2.
-int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed, void* workspace,
-                  size_t ws_bytes, void* stream, mlmc_result* out) {
+//
+// Sharded form (one rank per GPU): each pass,
+// rank r of W integrates its contiguous slice of every level's new path
+// range, the per-level sums (count, diverged, steps, the twelve FP64 sums and
+// an error flag) are summed over the ranks by the caller's all-reduce, and
+// every rank then takes the same N_l and bias-test decisions from the same
+// totals.  W = 1 without a reduce hook is mlmc_estimate.
+struct Shard {
+  int rank, world;
+  mlmc_allreduce_fn reduce;
+  void* ctx;
+};
+constexpr int kShardWidth = 16;  // doubles per level in the reduced buffer
+
+static int estimate_impl(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                         void* workspace, size_t ws_bytes, void* stream, mlmc_result* out,
+                         const Shard& sh) {
   if (!out || !p || !(eps > 0.0)) return MLMC_EINVAL;
   if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2)
     return MLMC_EINVAL;
+  if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world || (sh.world > 1 && !sh.reduce))
+    return MLMC_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
+  double buf[MLMC_MAX_LEVELS * kShardWidth];
   mlmc_level_result S[MLMC_MAX_LEVELS];
   uint64_t Ndone[MLMC_MAX_LEVELS] = {0}, dN[MLMC_MAX_LEVELS] = {0};
   double V[MLMC_MAX_LEVELS] = {0}, C[MLMC_MAX_LEVELS] = {0};
@@ -783,18 +802,42 @@ int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t see
   for (;;) {
     dN[L] = (uint64_t)p->n_init;
     for (int pass = 0; pass < 2; ++pass) {
+      int err = MLMC_OK;
       for (int l = lmin; l <= L; ++l) {
-        if (!dN[l]) continue;
+        double* b = buf + (l - lmin) * kShardWidth;
+        for (int k = 0; k < kShardWidth; ++k) b[k] = 0.0;
+        if (!dN[l] || err) continue;
+        // this rank's contiguous slice of [Ndone, Ndone + dN)
+        const uint64_t share = dN[l] / (uint64_t)sh.world, rem = dN[l] % (uint64_t)sh.world;
+        const uint64_t r_ = (uint64_t)sh.rank;
+        const uint64_t cnt = share + (r_ < rem ? 1 : 0);
+        const uint64_t first = Ndone[l] + r_ * share + (r_ < rem ? r_ : rem);
+        if (!cnt) continue;
         mlmc_level_result r;
-        int rc = mlmc_level_sums(l, dN[l], integrator, p, seed, Ndone[l], workspace, ws_bytes,
-                                 stream, &r);
-        if (rc == MLMC_ENONFINITE) status = MLMC_ENONFINITE;
-        else if (rc) return rc;
-        S[l].n += r.n;
-        S[l].n_nonfinite += r.n_nonfinite;
-        S[l].path_steps += r.path_steps;
+        int rc = mlmc_level_sums(l, cnt, integrator, p, seed, first, workspace, ws_bytes, stream,
+                                 &r);
+        if (rc && rc != MLMC_ENONFINITE) { err = rc; continue; }
+        b[0] = (double)r.n;
+        b[1] = (double)r.n_nonfinite;
+        b[2] = (double)r.path_steps;
         for (int q = 0; q < 2; ++q)
-          for (int k = 0; k < 6; ++k) S[l].sum[q][k] += r.sum[q][k];
+          for (int k = 0; k < 6; ++k) b[3 + 6 * q + k] = r.sum[q][k];
+      }
+      const int nl = L - lmin + 1;
+      buf[nl * kShardWidth - 1] = err ? 1.0 : 0.0;   // last slot of the last level: error flag
+      if (sh.world > 1) {
+        if (sh.reduce(buf, nl * kShardWidth, sh.ctx) != 0) return MLMC_ECOMM;
+      }
+      if (buf[nl * kShardWidth - 1] != 0.0) return err ? err : MLMC_ECOMM;  // a rank failed
+      for (int l = lmin; l <= L; ++l) {
+        const double* b = buf + (l - lmin) * kShardWidth;
+        if (!dN[l]) continue;
+        S[l].n += (uint64_t)b[0];
+        S[l].n_nonfinite += (uint64_t)b[1];
+        S[l].path_steps += (uint64_t)b[2];
+        for (int q = 0; q < 2; ++q)
+          for (int k = 0; k < 6; ++k) S[l].sum[q][k] += b[3 + 6 * q + k];
+        if (b[1] > 0.0) status = MLMC_ENONFINITE;
         Ndone[l] += dN[l];
         dN[l] = 0;
       }
@@ -850,6 +893,19 @@ int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t see
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (status) return status;
   return converged ? MLMC_OK : MLMC_ENOTCONV;
+}
+
+int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed, void* workspace,
+                  size_t ws_bytes, void* stream, mlmc_result* out) {
+  return estimate_impl(eps, integrator, p, seed, workspace, ws_bytes, stream, out,
+                       Shard{0, 1, nullptr, nullptr});
+}
+
+int mlmc_estimate_sharded(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                          int rank, int world, mlmc_allreduce_fn reduce, void* ctx,
+                          void* workspace, size_t ws_bytes, void* stream, mlmc_result* out) {
+  return estimate_impl(eps, integrator, p, seed, workspace, ws_bytes, stream, out,
+                       Shard{rank, world, reduce, ctx});
 }
 
 // Plain Monte Carlo (Eq. StMCestimator) at one timestep: a pilot run sets

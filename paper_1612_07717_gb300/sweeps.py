@@ -13,6 +13,9 @@ Both use FP32 paths with FP64 sums, so the step counts compare the two
 algorithms on equal terms.
 
 Run on a GPU: ``python -m paper_1612_07717_gb300.sweeps [out.json]``.
+``python -m paper_1612_07717_gb300.sweeps level se|gl|baoab LEVEL LOG2N X_ADAPT`` times
+one level-sums launch of the paper scenario (X_ADAPT 0: uniform timesteps),
+the unit a profiler capture of the level kernels is taken on.
 """
 import json
 import math
@@ -69,7 +72,31 @@ def adaptive_cost_sweep(eps_list=EPS, integrators=(SE, GL), x_adapt=0.05):
     return out
 
 
-if __name__ == "__main__":
+def time_level(integ, level, n, z_adapt=0.0, reps=3, seed=4):
+    """Time level_sums of n pairs on one level (the last of reps launches)."""
+    import torch
+    p = make_params(dict(W.PAPER, z_adapt=z_adapt), precision=FP32)
+    ws = Workspace(p)
+    from . import level_sums
+    for _ in range(reps - 1):
+        level_sums(level, n, integ, p, seed, workspace=ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s = level_sums(level, n, integ, p, seed, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return dict(level=level, pairs=n, z_adapt=z_adapt, path_steps=s["path_steps"], ms=ms,
+                path_steps_per_s=s["path_steps"] / (ms * 1e-3))
+
+
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
+    integ = {"se": SE, "gl": GL, "baoab": BAOAB}[sys.argv[2]]
+    print(json.dumps(time_level(integ, int(sys.argv[3]), 1 << int(sys.argv[4]),
+                                float(sys.argv[5]))))
+elif __name__ == "__main__":
     res = dict(scenario="paper (H = 1, u* = 0.2, T = 1, X0 = 0.05, U0 = 0.1, eps_reg = 0.01, M0 = 40)",
                cost=paper_cost_sweep(), adaptive=adaptive_cost_sweep())
     text = json.dumps(res, indent=1)
