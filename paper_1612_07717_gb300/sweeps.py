@@ -1,5 +1,6 @@
 """Cost against tolerance in the paper's scenario (Section 6.1, Fig.
-CostRatesPosition; Section 7.3 for adaptive timesteps).
+CostRatesPosition; Section 7.3 for adaptive timesteps; Section 6.3's table of
+the binned density's cost for three release heights).
 
 For each RMSE tolerance eps on E[X_T] and each integrator:
 
@@ -22,8 +23,8 @@ import math
 import sys
 import time
 
-from . import (BAOAB, FP32, GL, SE, Workspace, estimate, estimate_graph, make_params,
-               stmc_estimate)
+from . import (BAOAB, FP32, GL, SE, Workspace, estimate, estimate_graph, estimate_pdf,
+               level_pdf_sums, make_params, stmc_estimate)
 from . import workloads as W
 
 NAMES = {SE: "SE", GL: "GL", BAOAB: "BAOAB"}
@@ -72,6 +73,64 @@ def adaptive_cost_sweep(eps_list=EPS, integrators=(SE, GL), x_adapt=0.05):
     return out
 
 
+def _pdf_params(integ, x0, level_min=0):
+    # Section 6.3: r = 4, delta = 0.1, M0 = 80 for SE and GL, 40 for BAOAB
+    return make_params(dict(W.PAPER, z0=x0, M0=40 if integ == BAOAB else 80, smooth_r=4,
+                            smooth_delta=0.1, n_init=4000, L_max=12, level_min=level_min),
+                       precision=FP32)
+
+
+def stmc_pdf(eps, integ, x0, level, k=20, seed=6, n_pilot=4000):
+    """Plain Monte Carlo for the k-bin density at level's timestep: a pilot
+    run, then N = 2 max_i Var[P_i] / eps^2 paths in total."""
+    import torch
+    p = _pdf_params(integ, x0, level_min=level)
+    ws = Workspace(p)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    a = level_pdf_sums(level, n_pilot, integ, p, seed, k, workspace=ws)
+    n = a["n"]
+    v = max(max(s2 / n - (s1 / n) ** 2, 0.0) for s1, s2 in a["sum"])
+    N = max(n_pilot, int(math.ceil(2.0 * v / eps ** 2)))
+    sums = [list(x) for x in a["sum"]]
+    if N > n_pilot:
+        b = level_pdf_sums(level, N - n_pilot, integ, p, seed, k, path_offset=n_pilot,
+                           workspace=ws)
+        sums = [[x[0] + y[0], x[1] + y[1]] for x, y in zip(sums, b["sum"])]
+        n += b["n"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    M = p.M0 << level
+    return dict(level=level, N=n, path_steps=N * M, seconds=dt, pdf=[s[0] / n for s in sums])
+
+
+def pdf_release_table(eps_density=4e-3, k=20, releases=(0.05, 0.1, 0.2), seed=5):
+    """Section 6.3's table: cost of the 20-bin density to RMSE eps_density
+    for release heights 0.05, 0.1, 0.2 -- MLMC (SE, GL, BAOAB) and plain
+    Monte Carlo at the MLMC hierarchy's finest timestep.  The tolerance is on
+    the density rho = P_i / (H / k); the estimators return the bins'
+    probabilities P_i, so they run at eps = eps_density H / k."""
+    import torch
+    eps = eps_density * W.PAPER["H"] / k
+    out = []
+    for x0 in releases:
+        for integ in (SE, GL, BAOAB):
+            p = _pdf_params(integ, x0)
+            ws = Workspace(p)
+            estimate_pdf(eps * 2, integ, p, seed + 1, k, workspace=ws)      # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = estimate_pdf(eps, integ, p, seed, k, workspace=ws)
+            dt = time.perf_counter() - t
+            m = dict(L=r["L"], converged=r["converged"], N=r["N"],
+                     path_steps=r["total_path_steps"], seconds=dt, mass=sum(r["pdf"]))
+            s = stmc_pdf(eps, integ, x0, r["L"], k)
+            out.append(dict(release=x0, integrator=NAMES[integ], mlmc=m,
+                            stmc=dict(level=s["level"], N=s["N"], path_steps=s["path_steps"],
+                                      seconds=s["seconds"])))
+    return out
+
+
 def time_level(integ, level, n, z_adapt=0.0, reps=3, seed=4):
     """Time level_sums of n pairs on one level (the last of reps launches)."""
     import torch
@@ -98,7 +157,8 @@ if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
                                 float(sys.argv[5]))))
 elif __name__ == "__main__":
     res = dict(scenario="paper (H = 1, u* = 0.2, T = 1, X0 = 0.05, U0 = 0.1, eps_reg = 0.01, M0 = 40)",
-               cost=paper_cost_sweep(), adaptive=adaptive_cost_sweep())
+               cost=paper_cost_sweep(), adaptive=adaptive_cost_sweep(),
+               pdf=pdf_release_table())
     text = json.dumps(res, indent=1)
     if len(sys.argv) > 1:
         with open(sys.argv[1], "w") as f:

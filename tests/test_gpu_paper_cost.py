@@ -7,7 +7,9 @@
 * plain Monte Carlo with the splitting methods is much cheaper than with SE
   (the paper: GL about 5x, BAOAB more than 20x), because their bias at a
   given h is 13x and 52x smaller;
-* MLMC beats plain Monte Carlo at the tightest tolerance.
+* MLMC beats plain Monte Carlo at the tightest tolerance;
+* the binned density's cost table of Section 6.3 (release heights 0.05,
+  0.1, 0.2), in path-steps.
 """
 import numpy as np
 import pytest
@@ -54,3 +56,37 @@ def test_integrator_comparison(sweep):
     assert s["SE"] / s["BAOAB"] > 8, s
     L = {n: sweep["%s/%g" % (n, e)]["mlmc"]["L"] for n in ("SE", "GL", "BAOAB")}
     assert L["SE"] > L["GL"] >= L["BAOAB"], L
+
+
+@pytest.fixture(scope="module")
+def pdf_table():
+    return {(r["release"], r["integrator"]): r for r in sweeps.pdf_release_table()}
+
+
+def test_pdf_release_table_of_section_6_3(pdf_table):
+    """The 20-bin density to RMSE 4e-3 on rho (Section 6.3's table): plain
+    Monte Carlo with SE grows steeply as the release height falls while GL
+    and BAOAB barely move; MLMC-SE beats StMC-SE everywhere and gets cheaper
+    with height; StMC-BAOAB is the cheapest at 0.05 and MLMC-SE at 0.2."""
+    st = {k: r["stmc"]["path_steps"] for k, r in pdf_table.items()}
+    ml = {k: r["mlmc"]["path_steps"] for k, r in pdf_table.items()}
+    assert all(r["mlmc"]["converged"] == 1 for r in pdf_table.values())
+    assert st[(0.05, "SE")] > 3 * st[(0.2, "SE")]
+    for name in ("GL", "BAOAB"):
+        v = [st[(x, name)] for x in (0.05, 0.1, 0.2)]
+        assert max(v) < 1.6 * min(v), (name, v)
+    assert st[(0.05, "SE")] > 4 * st[(0.05, "GL")]
+    assert st[(0.05, "SE")] > 10 * st[(0.05, "BAOAB")]
+    for x in (0.05, 0.1, 0.2):
+        assert ml[(x, "SE")] * 5 < st[(x, "SE")], x
+    assert ml[(0.05, "SE")] > 1.3 * ml[(0.1, "SE")]
+    assert ml[(0.1, "SE")] > 1.3 * ml[(0.2, "SE")]
+    everything = lambda x: {**{("stmc", n): st[(x, n)] for n in ("SE", "GL", "BAOAB")},
+                            **{("mlmc", n): ml[(x, n)] for n in ("SE", "GL", "BAOAB")}}
+    low = everything(0.05)
+    assert min(low, key=low.get) == ("stmc", "BAOAB"), low
+    high = everything(0.2)
+    assert high[("mlmc", "SE")] <= 1.2 * high[("stmc", "BAOAB")], high
+    # the bins hold the probability mass that the smoothing keeps inside [0, H]
+    for r in pdf_table.values():
+        assert 0.9 < r["mlmc"]["mass"] <= 1.0 + 1e-3
