@@ -32,9 +32,13 @@ N0 = 1e9
 # of fine steps: 3 BAOAB steps, the coarse coupling 9 and one Box-Muller pair
 # 13 -> 181 / 3 path-steps.
 FLOPS_PER_PATH_STEP = 181.0 / 3.0
-# DRAM bytes per launch of the path kernel from an ncu capture, valid only
-# for the kernel sources it was taken with (their SHA-1, see kernel_sha1).
-TRAFFIC = {"kernel_sha1": "c3016a711852b3672a99e63814110109403ed03f", "bytes_per_launch": 0.912e6}
+# ncu figures of the path kernel, valid only for the kernel sources they were
+# taken with (their SHA-1, see kernel_sha1): DRAM bytes per full-size launch
+# (launch list) and, from the full capture of the 1e8-path case, the FMA-pipe
+# and issue-slot activity and the thread instructions per path-step.
+TRAFFIC = {"kernel_sha1": "c3016a711852b3672a99e63814110109403ed03f", "bytes_per_launch": 0.912e6,
+           "fma_pipe_active_pct": 54.8, "issue_active_pct": 68.5,
+           "thread_inst_per_path_step": 70.8}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
@@ -373,7 +377,15 @@ def main():
                                      if TRAFFIC["kernel_sha1"] == kernel_sha1() else None),
                          "peak_source": "measured FFMA probe" if peak_probe else
                          "derived SMs*128*2*clock at %.0f MHz" % sm_mhz,
-                         "flops_per_path_step": FLOPS_PER_PATH_STEP},
+                         "flops_per_path_step": FLOPS_PER_PATH_STEP,
+                         "ncu": ({k: TRAFFIC[k] for k in ("fma_pipe_active_pct", "issue_active_pct",
+                                                          "thread_inst_per_path_step")}
+                                 if TRAFFIC["kernel_sha1"] == kernel_sha1() else None),
+                         # one instruction per SM sub-partition per cycle at the
+                         # sampled clock: the path-steps/s the issue slots allow
+                         "issue_ceiling_path_steps_per_s": (
+                             info["sms"] * 4 * sm_mhz * 1e6 * 32 / TRAFFIC["thread_inst_per_path_step"]
+                             if TRAFFIC["kernel_sha1"] == kernel_sha1() else None)},
             "e2e": {"value": world * steps_per_step / e2e_s, "unit": "path-steps/s",
                     "h2d_bytes_per_step": C.sizeof(G.LevelRequest) * n_req + C.sizeof(G.Params),
                     "d2h_bytes_per_step": C.sizeof(G.LevelResult) * n_req},
