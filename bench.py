@@ -307,8 +307,9 @@ def main():
         launch.run(stream)
     torch.cuda.synchronize()
 
-    clk_file = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
-    os.makedirs(os.path.dirname(clk_file), exist_ok=True)
+    import tempfile
+    clk_file = os.path.join(tempfile.gettempdir(),
+                            "mlmc_bench_clocks_rank%d_%d.csv" % (rank, os.getpid()))
     sampler = sample_clocks(None, clk_file) if rank == 0 else None
     time.sleep(0.3)
     if world > 1:
