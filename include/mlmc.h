@@ -108,7 +108,7 @@ typedef struct mlmc_params {
                            (the paper's min(h, lambda(X_adapt) / lambda(X_n) h)
                            rounded down to a 1024th of h), the coupled pair is
                            driven on the merged time grid.  SE and GL only;
-                           needs 0 < z_adapt <= H, M_l <= 2^21 on the levels
+                           needs 0 < z_adapt <= H, M_l <= 2^20 on the levels
                            used, and lambda(X_adapt) >= lambda_max / 1024.
                            Supported by the level-sums, multi-level, estimate
                            and path entry points; the graph, server, density
@@ -253,7 +253,9 @@ int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int n_req, int 
  * sample-size rule of Giles 2008 the paper adopts in Section 6): levels are
  * added from level_min, N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k
  * C_k)), converged when max(|Yhat_{L-1}| / 2, |Yhat_L|) < eps / sqrt(2).
- * Host-driven loop of mlmc_level_sums calls on `stream`. */
+ * Host-driven loop on `stream`: each pass (the new level's n_init samples,
+ * then the top-up of every level) is one mlmc_multilevel_sums launch over
+ * the levels that need samples. */
 int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed,
                   void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
 

@@ -3,6 +3,13 @@
 // kernel and per-pair outputs, for FP32 and FP64 paths.  They reuse the
 // accumulators, reductions and planning of the uniform kernels; each adds
 // the integrator steps it took to its partial sums.
+//
+// Pairs take very different numbers of steps, so a block hands its pairs to
+// its threads dynamically: a chunk of pairs is claimed one at a time from a
+// shared counter, each finished pair's end state is parked in shared memory
+// at the pair's own slot, and once the chunk is done the threads add the
+// slots in a fixed order (thread t: slots t, t + 256, ...).  The sums are
+// therefore independent of which thread ran which pair.
 #define MLMC_KNS k_adapt
 #include "mlmc_kernels.cuh"
 #include "mlmc_adaptive.cuh"
@@ -10,30 +17,56 @@
 namespace mlmc {
 namespace k_adapt {
 
-// The thread's pairs first + k, k = begin, begin + stride, ... < end, run
-// back to back: a finished pair is summed and the next one started at the
-// following round.  Every thread of the warp calls this (the loop condition
-// is a warp vote).
+// Pairs per chunk and the shared memory that parks their end states:
+// z_f, z_c (path precision) and the steps with the diverged mark in bit 31.
+template <typename R>
+struct ChunkOf {
+  static constexpr uint32_t kPairs = sizeof(R) == 4 ? 4096u : 2048u;
+  static constexpr size_t kBytes = (size_t)kPairs * (2 * sizeof(R) + sizeof(uint32_t));
+};
+
+// Pairs [first, first + count) of one level, run by the whole block.  Every
+// thread of the block calls this (it synchronises the block).
 template <int INTEG, typename R, bool COUPLED>
-__device__ __forceinline__ void adapt_lane(const Model<R>& m, const Level<R>& lv, uint64_t first,
-                                           uint64_t begin, uint64_t end, uint64_t stride,
-                                           Acc& acc) {
-  uint64_t k = begin;
-  bool active = k < end;
-  APair<R> P;
-  if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
-  while (__any_sync(0xFFFFFFFFu, active)) {
-    if (active) {
-      apair_round<INTEG, R, COUPLED>(m, P);
-      if (apair_done(P)) {
-        apair_finish<R, COUPLED>(P);
-        acc_add<R, COUPLED>(acc, m, P.f.z, P.c.z, P.bad);
-        acc.steps += P.nf + P.nc;
-        k += stride;
-        active = k < end;
-        if (active) apair_init<R, COUPLED>(m, lv, first + k, P);
+__device__ __forceinline__ void adapt_block(const Model<R>& m, const Level<R>& lv, uint64_t first,
+                                            uint64_t count, Acc& acc) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  R* s_zf = (R*)s_dyn;
+  R* s_zc = s_zf + ChunkOf<R>::kPairs;
+  uint32_t* s_info = (uint32_t*)(s_zc + ChunkOf<R>::kPairs);
+  __shared__ unsigned int s_next;
+  for (uint64_t base = 0; base < count; base += ChunkOf<R>::kPairs) {
+    const uint32_t n = (uint32_t)(count - base < ChunkOf<R>::kPairs ? count - base
+                                                                    : ChunkOf<R>::kPairs);
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    uint32_t k = atomicAdd(&s_next, 1u);
+    bool active = k < n;
+    APair<R> P;
+    if (active) apair_init<R, COUPLED>(m, lv, first + base + k, P);
+    // a finished pair is parked and the next one started at the next round;
+    // the loop condition is a warp vote, so every lane of the warp runs it
+    while (__any_sync(0xFFFFFFFFu, active)) {
+      if (active) {
+        apair_round<INTEG, R, COUPLED>(m, P);
+        if (apair_done(P)) {
+          apair_finish<R, COUPLED>(P);
+          s_zf[k] = P.f.z;
+          s_zc[k] = P.c.z;
+          s_info[k] = (P.nf + P.nc) | (P.bad ? 0x80000000u : 0u);
+          k = atomicAdd(&s_next, 1u);
+          active = k < n;
+          if (active) apair_init<R, COUPLED>(m, lv, first + base + k, P);
+        }
       }
     }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      const uint32_t info = s_info[j];
+      acc_add<R, COUPLED>(acc, m, s_zf[j], s_zc[j], (info >> 31) != 0);
+      acc.steps += info & 0x7FFFFFFFu;
+    }
+    __syncthreads();
   }
 }
 
@@ -41,9 +74,11 @@ template <int INTEG, typename R, bool COUPLED>
 __global__ void __launch_bounds__(kBlock) k_adapt_sums(const __grid_constant__ SumsArgs<R> a) {
   Acc acc;
   acc_zero(acc, a.m.qoi1_mode != 0);
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  adapt_lane<INTEG, R, COUPLED>(a.m, a.lv, a.offset,
-                                (uint64_t)blockIdx.x * kBlock + threadIdx.x, a.N, stride, acc);
+  // block b takes the contiguous pairs [b per, (b + 1) per)
+  const uint64_t per = (a.N + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * per;
+  const uint64_t hi = lo + per < a.N ? lo + per : a.N;
+  adapt_block<INTEG, R, COUPLED>(a.m, a.lv, a.offset + lo, hi > lo ? hi - lo : 0, acc);
   block_reduce_store(acc, COUPLED, a.m.qoi1_mode != 0, a.partials + blockIdx.x);
 }
 
@@ -66,10 +101,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_adapt_multil
     const Level<R> lv = rq.lv;
     Acc acc;
     acc_zero(acc, a.m.qoi1_mode != 0);
-    if (lv.coupled)
-      adapt_lane<INTEG, R, true>(a.m, lv, rq.first + start, threadIdx.x, count, kBlock, acc);
-    else
-      adapt_lane<INTEG, R, false>(a.m, lv, rq.first + start, threadIdx.x, count, kBlock, acc);
+    if (lv.coupled) adapt_block<INTEG, R, true>(a.m, lv, rq.first + start, count, acc);
+    else adapt_block<INTEG, R, false>(a.m, lv, rq.first + start, count, acc);
     block_reduce_store(acc, lv.coupled != 0, a.m.qoi1_mode != 0, a.partials + it);
   }
 }
@@ -101,6 +134,14 @@ __global__ void __launch_bounds__(kBlock) k_adapt_paths(const __grid_constant__ 
   }
 }
 
+// Launch with `smem` bytes of dynamic shared memory (above the default 48 KB
+// limit when the chunk needs it).
+template <typename K, typename Args>
+void launch_with_smem(K kernel, int grid, size_t smem, cudaStream_t st, const Args& a) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kernel<<<grid, kBlock, smem, st>>>(a);
+}
+
 template <typename R>
 cudaError_t sums(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N, uint64_t offset,
                  Partial* partials, int grid, cudaStream_t st) {
@@ -110,12 +151,13 @@ cudaError_t sums(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N
   a.N = N;
   a.offset = offset;
   a.partials = partials;
+  const size_t smem = ChunkOf<R>::kBytes;
   if (integ == kSE) {
-    if (ls.coupled) k_adapt_sums<kSE, R, true><<<grid, kBlock, 0, st>>>(a);
-    else k_adapt_sums<kSE, R, false><<<grid, kBlock, 0, st>>>(a);
+    if (ls.coupled) launch_with_smem(k_adapt_sums<kSE, R, true>, grid, smem, st, a);
+    else launch_with_smem(k_adapt_sums<kSE, R, false>, grid, smem, st, a);
   } else if (integ == kGL) {
-    if (ls.coupled) k_adapt_sums<kGL, R, true><<<grid, kBlock, 0, st>>>(a);
-    else k_adapt_sums<kGL, R, false><<<grid, kBlock, 0, st>>>(a);
+    if (ls.coupled) launch_with_smem(k_adapt_sums<kGL, R, true>, grid, smem, st, a);
+    else launch_with_smem(k_adapt_sums<kGL, R, false>, grid, smem, st, a);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -141,8 +183,9 @@ cudaError_t multilevel(int integ, const HostModel& hm, const ReqPlan* plan, int 
   a.n_items = n_items;
   a.partials = partials;
   a.counter = counter;
-  if (integ == kSE) k_adapt_multilevel<kSE, R><<<grid, kBlock, 0, st>>>(a);
-  else if (integ == kGL) k_adapt_multilevel<kGL, R><<<grid, kBlock, 0, st>>>(a);
+  const size_t smem = ChunkOf<R>::kBytes;
+  if (integ == kSE) launch_with_smem(k_adapt_multilevel<kSE, R>, grid, smem, st, a);
+  else if (integ == kGL) launch_with_smem(k_adapt_multilevel<kGL, R>, grid, smem, st, a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -769,6 +769,7 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
 //   sqrt(V_l / C_l) sum_k sqrt(V_k C_k));  4. run the extra samples;
 //   5. if L >= level_min + 2 stop when max(|Yhat_{L-1}| / 2, |Yhat_L|) <
 //   eps / sqrt(2);  6. else L += 1 (up to L_max) and go to 2.
+// Each pass of steps 2 and 4 is one batched multi-level launch.
 //
 // Sharded form (one rank per GPU): each pass,
 // rank r of W integrates its contiguous slice of every level's new path
@@ -802,26 +803,39 @@ static int estimate_impl(double eps, int integrator, const mlmc_params* p, uint6
   for (;;) {
     dN[L] = (uint64_t)p->n_init;
     for (int pass = 0; pass < 2; ++pass) {
+      // this rank's contiguous slice of every level's [Ndone, Ndone + dN),
+      // all levels of the pass in one multi-level launch
       int err = MLMC_OK;
+      mlmc_level_request rq[MLMC_MAX_LEVELS];
+      int nrq = 0;
       for (int l = lmin; l <= L; ++l) {
         double* b = buf + (l - lmin) * kShardWidth;
         for (int k = 0; k < kShardWidth; ++k) b[k] = 0.0;
-        if (!dN[l] || err) continue;
-        // this rank's contiguous slice of [Ndone, Ndone + dN)
+        if (!dN[l]) continue;
         const uint64_t share = dN[l] / (uint64_t)sh.world, rem = dN[l] % (uint64_t)sh.world;
         const uint64_t r_ = (uint64_t)sh.rank;
         const uint64_t cnt = share + (r_ < rem ? 1 : 0);
         const uint64_t first = Ndone[l] + r_ * share + (r_ < rem ? r_ : rem);
         if (!cnt) continue;
-        mlmc_level_result r;
-        int rc = mlmc_level_sums(l, cnt, integrator, p, seed, first, workspace, ws_bytes, stream,
-                                 &r);
-        if (rc && rc != MLMC_ENONFINITE) { err = rc; continue; }
-        b[0] = (double)r.n;
-        b[1] = (double)r.n_nonfinite;
-        b[2] = (double)r.path_steps;
-        for (int q = 0; q < 2; ++q)
-          for (int k = 0; k < 6; ++k) b[3 + 6 * q + k] = r.sum[q][k];
+        rq[nrq].level = l;
+        rq[nrq].reserved = 0;
+        rq[nrq].first = first;
+        rq[nrq].count = cnt;
+        ++nrq;
+      }
+      if (nrq) {
+        mlmc_level_result res[MLMC_MAX_LEVELS];
+        int rc = mlmc_multilevel_sums(rq, nrq, integrator, p, seed, workspace, ws_bytes, stream,
+                                      res);
+        if (rc && rc != MLMC_ENONFINITE) err = rc;
+        for (int k = 0; k < nrq && !err; ++k) {
+          double* b = buf + (rq[k].level - lmin) * kShardWidth;
+          b[0] = (double)res[k].n;
+          b[1] = (double)res[k].n_nonfinite;
+          b[2] = (double)res[k].path_steps;
+          for (int q = 0; q < 2; ++q)
+            for (int j = 0; j < 6; ++j) b[3 + 6 * q + j] = res[k].sum[q][j];
+        }
       }
       const int nl = L - lmin + 1;
       buf[nl * kShardWidth - 1] = err ? 1.0 : 0.0;   // last slot of the last level: error flag

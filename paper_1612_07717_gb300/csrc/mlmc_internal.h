@@ -39,8 +39,8 @@ struct HostModel {
   double z_adapt, lam_a;              // X_adapt and lambda(X_adapt)
 };
 // Adaptive timesteps count time in units of h_l / 1024 of the level: T is
-// 1024 M_l units, which must stay below 2^31.
-constexpr int64_t kAdaptMaxM = (int64_t)1 << 21;
+// 1024 M_l units, and a pair's steps (at most 1536 M_l) must fit 31 bits.
+constexpr int64_t kAdaptMaxM = (int64_t)1 << 20;
 // Coefficients of the smoothing polynomial p_r (Section 5.1); 0 or -1.
 int smooth_coefficients(int r, double* c);
 
