@@ -671,7 +671,8 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
   // about items_per_block items per resident block, bounded by kMaxItems
   double target = total / ((double)items_per_block(p->precision, integ) * (double)grid);
   if (target < 1.0) target = 1.0;
-  const uint64_t min_paths = min_item_paths(p->precision, integ);
+  // the adaptive kernels run one pair per thread at a time
+  const uint64_t min_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
   uint64_t items = 0;
   for (int pass = 0; pass < 40; ++pass) {
     items = 0;
@@ -1087,7 +1088,8 @@ static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int
   }
   double target = total / (16.0 * (double)grid);
   if (target < 1.0) target = 1.0;
-  const uint64_t min_paths = min_item_paths(p->precision, integ);
+  // the adaptive kernels run one pair per thread at a time
+  const uint64_t min_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
   for (int pass = 0; pass < 64; ++pass) {
     uint64_t items = 0;
     bool too_big = false;
