@@ -184,9 +184,19 @@ def cpu_baseline_sample():
     for l, n in sched:
         O.level_sums(po, INTEGRATOR, l, n, 0, 1, threads=threads)
     dt = time.perf_counter() - t
+    # one core, on a sixteenth of the sample
+    sched1 = [(l, max(1, int(round(n * ORACLE_SAMPLE_SCALE / 16)))) for l, n in workload()]
+    steps1 = path_steps_of(sched1)
+    t = time.perf_counter()
+    for l, n in sched1:
+        O.level_sums(po, INTEGRATOR, l, n, 0, 1, threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": steps / dt, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
             "sample": "levels 0..12 of the same workload with N_l x %g (%d path-steps, %.1f s)"
-                      % (ORACLE_SAMPLE_SCALE, steps, dt)}
+                      % (ORACLE_SAMPLE_SCALE, steps, dt),
+            "single_core": {"value": steps1 / dt1, "unit": "path-steps/s", "cores": 1,
+                            "sample": "N_l x %g (%d path-steps, %.1f s)"
+                                      % (ORACLE_SAMPLE_SCALE / 16, steps1, dt1)}}
 
 
 def time_to_eps(G, W, torch, eps_frac=2.0 ** -10):
