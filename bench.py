@@ -36,7 +36,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # taken with (their SHA-1, see kernel_sha1): DRAM bytes per full-size launch
 # (launch list) and, from the full capture of the 1e8-path case, the FMA-pipe
 # and issue-slot activity and the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "c3016a711852b3672a99e63814110109403ed03f", "bytes_per_launch": 0.912e6,
+TRAFFIC = {"kernel_sha1": "5065ad5189d327e9b98be85b19fef964cd7d9975", "bytes_per_launch": 0.918e6,
            "fma_pipe_active_pct": 54.8, "issue_active_pct": 68.5,
            "thread_inst_per_path_step": 70.8}
 # The sources the persistent FP32 path kernels are compiled from.

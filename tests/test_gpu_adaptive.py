@@ -200,3 +200,19 @@ def test_adaptive_is_refused_where_unsupported():
     with pytest.raises(G.MLMCError) as e:     # lambda(X_adapt) below lambda_max / 1024
         G.level_sums(2, 100, G.GL, gpu_params(dict(d, z_adapt=599.9)), 1)
     assert e.value.code == G.EINVAL
+
+
+@pytest.mark.parametrize("integ", [G.SE, G.GL])
+def test_adaptive_empty_single_and_ragged(integ):
+    # FP64 paths, which equal the oracle's pair by pair
+    d = CASES[0][1] if integ == G.SE else CASES[2][1]
+    level = d["level_min"] + 1
+    pg, po = gpu_params(d, G.FP64), oracle_params(d, G.FP64)
+    s0 = G.level_sums(level, 0, integ, pg, 3)
+    assert s0["n"] == 0 and s0["path_steps"] == 0
+    for n, off in ((1, 12345), (4096 * 2 + 257, 7)):   # not a multiple of a chunk or a block
+        s = G.level_sums(level, n, integ, pg, 3, path_offset=off)
+        o = O.level_sums(po, integ, level, n, off, 3)
+        assert s["n"] == o["n"] == n and s["path_steps"] == o["path_steps"]
+        assert np.array_equal(np.array(s["sum"][1]), o["sum"][1])     # indicator counts
+        assert np.allclose(s["sum"][0], o["sum"][0], rtol=1e-9, atol=1e-9 * n)
