@@ -29,7 +29,8 @@
  *    output is valid unless stated.  mlmc_strerror() names the code.
  *  - Random numbers: Philox4x32-10 with key = seed and counter =
  *    (step_block, path_lo, path_hi ^ (level << 24), stream_id); fine step n
- *    of a path uses word n mod 4 of block n / 4, Box-Muller on word pairs.
+ *    of a path (with adaptive timesteps: merged interval n of the pair)
+ *    uses word n mod 4 of block n / 4, Box-Muller on word pairs.
  *    A path's samples therefore depend only on (seed, stream_id, level, path
  *    index): splitting [0, N) into calls over [0, a) and [a, N) with
  *    path_offset gives the same paths.
