@@ -344,22 +344,28 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  *                        pinned host staging buffers
  *   mlmc_server_submit   validates and queues a query; returns its id
  *   mlmc_server_tick     admits queued queries while a slot is free, runs
- *                        ONE persistent launch over the pending samples of
- *                        every active query (as many whole queries as the
- *                        tick's 2048 requests / 32768 work items allow),
- *                        reduces each request in item order, advances each
- *                        query's driver and retires finished queries;
- *                        synchronises the stream.  n_done: queries finished
- *                        in this tick; n_active: queries left (active and
- *                        queued)
+ *                        ONE persistent launch over chunks (at most 2^26
+ *                        path-steps each) of the active queries' pending
+ *                        passes -- least pending work first, a waiting
+ *                        query's priority doubling every tick -- up to
+ *                        2^28 path-steps, 2048 requests and 32768 work
+ *                        items per tick (always at least one chunk);
+ *                        reduces each chunk in item order, folds chunks
+ *                        into their queries in chunk order, advances the
+ *                        driver of every query whose pass is complete and
+ *                        retires finished queries; synchronises the stream.
+ *                        n_done: queries finished in this tick; n_active:
+ *                        queries left (active and queued)
  *   mlmc_server_poll     1 while the query runs; its final status (MLMC_OK,
  *                        MLMC_ENOTCONV, MLMC_ENONFINITE) with the result and
  *                        its submit-to-finish latency once done
  *   mlmc_server_release  forgets a finished query
  *   mlmc_server_stats    out = {ticks, finished, path-steps, busy seconds,
  *                        active, queued}
- * A request's split into work items depends only on that request, so a
- * query's result is bitwise the same alone and in any mix. */
+ * A pass's chunks, their split into work items and their folding order
+ * depend only on the query (and the server's grid), so a query's result is
+ * bitwise the same alone and in any mix; the budget decides only when a
+ * chunk runs. */
 typedef struct mlmc_server_s* mlmc_server;
 size_t mlmc_server_workspace_bytes(int max_active);
 int mlmc_server_create(int integrator, int precision, int max_active, uint64_t seed,

@@ -2,17 +2,25 @@
 //
 // Each query is one adaptive MLMC estimate (Giles 2008, Section 5, the rule
 // the paper adopts in its Section 6) of its own scenario (u*, H, z0, T, eps).
-// A query holds a device slot (its Model) while active.  Every tick the
-// server gathers the pending sample requests of all active queries into one
-// request table, runs ONE persistent multi-level launch over all of them,
-// reduces each request in item order, and advances each query's driver;
-// finished queries release their slot and queued queries are admitted in
-// arrival order when a slot and the tick's item budget allow.
+// A query holds a device slot (its Model) while active.  A pass of a query's
+// driver (the n_init samples of a new level, or the extra samples its
+// variance estimate asks for) is cut into chunks of at most kChunkSteps
+// path-steps; every tick the server fills ONE request table with chunks of
+// the active queries -- the query with the least work left in its pass
+// first, up to kTickSteps path-steps in all -- runs one persistent
+// multi-level launch over it, reduces each chunk in item order, folds the
+// chunks into their queries in chunk order, and advances a query's driver
+// once its pass is complete.  Finished queries release their slot and queued
+// queries are admitted in arrival order while a slot is free.  Light queries
+// therefore do not wait behind a heavy query's whole pass, and a tick stays
+// short however many heavy queries are active.
 //
-// A request's split into work items depends only on the request (a fixed
-// path-step target per item), and each request's items are reduced in item
-// order, so a query's sums -- and therefore its estimate -- are bitwise the
-// same whether it runs alone or among other queries.
+// The chunks of a pass, a chunk's split into work items and the order in
+// which chunks are folded depend only on the query (and the server's grid),
+// never on what else is active, so a query's sums -- and its estimate -- are
+// bitwise the same alone and among other queries; the tick budget decides
+// only WHEN a chunk runs.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -25,8 +33,10 @@
 namespace mlmc {
 
 constexpr int kMaxTableReq = 2048;          // requests per tick
-constexpr double kItemTarget = 1 << 20;     // path-steps per work item
-constexpr uint64_t kMaxItemsPerReq = 1024;  // items one request may use (32 levels fit one tick)
+constexpr double kItemTarget = 1 << 20;     // largest work item, path-steps
+constexpr uint64_t kMaxItemsPerReq = 1024;  // items one request may use
+constexpr double kChunkSteps = 1 << 26;     // path-steps of one chunk (one request)
+constexpr double kTickSteps = 1 << 28;      // path-steps of one tick (at least one chunk)
 constexpr size_t kModelSlot = 512;          // bytes reserved per Model
 constexpr int kQLevels = MLMC_MAX_LEVELS;
 
@@ -38,7 +48,9 @@ struct Query {
   int slot = -1;
   int state = 0;  // 0 queued, 1 active, 2 done
   int L = 0, pass = 0, converged = 0;
+  // Ndone: samples folded; dN: samples of the current pass not yet issued
   uint64_t Ndone[kQLevels] = {0}, dN[kQLevels] = {0};
+  int skipped = 0;  // ticks in a row this query waited with work pending
   uint64_t n[kQLevels] = {0}, bad[kQLevels] = {0}, steps[kQLevels] = {0};
   double S[kQLevels][2][6] = {};
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -125,32 +137,45 @@ static void q_result(Query& q) {
   q.status = out.n_nonfinite ? MLMC_ENONFINITE : (out.converged ? MLMC_OK : MLMC_ENOTCONV);
 }
 
-// Requests of one query for this tick (finest level first).
-static void q_plan(const Query& q, uint64_t min_item, std::vector<PlanReq>& out,
-                   uint64_t& items) {
-  for (int l = q.L; l >= q.p.level_min; --l) {
-    if (!q.dN[l]) continue;
-    const uint64_t spp = q_steps(q, l);
-    const double ppi = std::floor(kItemTarget / (double)spp);
-    uint64_t item_paths = ppi < (double)min_item ? min_item : (uint64_t)ppi;
-    const uint64_t min_paths = (q.dN[l] + kMaxItemsPerReq - 1) / kMaxItemsPerReq;
-    if (item_paths < min_paths) item_paths = min_paths;
-    if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
-    PlanReq r;
-    r.level = l;
-    r.coupled = l > q.p.level_min;
-    r.M = (int64_t)q.p.M0 << l;
-    r.h = q.p.T / (double)r.M;
-    r.first = q.Ndone[l];
-    r.count = q.dN[l];
-    r.path_steps = q.dN[l] * spp;
-    r.item_paths = (uint32_t)item_paths;
-    r.n_items = (uint32_t)((q.dN[l] + item_paths - 1) / item_paths);
-    r.item_base = 0;
-    r.slot = (uint32_t)q.slot;
-    items += r.n_items;
-    out.push_back(r);
-  }
+// Paths of one chunk of level l: kChunkSteps worth, at least one full item.
+static uint64_t chunk_paths(const Query& q, int l, uint64_t min_item) {
+  const double c = std::floor(kChunkSteps / (double)q_steps(q, l));
+  return c < (double)min_item ? min_item : (uint64_t)c;
+}
+
+static double pending_steps(const Query& q) {
+  double w = 0.0;
+  for (int l = q.p.level_min; l <= q.L; ++l) w += (double)q.dN[l] * (double)q_steps(q, l);
+  return w;
+}
+
+// The request of the chunk of `count` samples starting at `first` on level
+// l.  Its items spread the chunk over the grid (so a lone light chunk still
+// fills the GPU), with at least min_item and at most kItemTarget path-steps'
+// worth of paths each.  Depends only on (query, level, first, count, grid).
+static PlanReq chunk_request(const Query& q, int l, uint64_t first, uint64_t count,
+                             uint64_t min_item, int grid) {
+  const uint64_t spp = q_steps(q, l);
+  const double cap_d = std::floor(kItemTarget / (double)spp);
+  const uint64_t cap = cap_d < (double)min_item ? min_item : (uint64_t)cap_d;
+  const uint64_t want = (count + (uint64_t)grid - 1) / (uint64_t)grid;
+  uint64_t item_paths = want < min_item ? min_item : (want > cap ? cap : want);
+  const uint64_t min_paths = (count + kMaxItemsPerReq - 1) / kMaxItemsPerReq;
+  if (item_paths < min_paths) item_paths = min_paths;
+  if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
+  PlanReq r;
+  r.level = l;
+  r.coupled = l > q.p.level_min;
+  r.M = (int64_t)q.p.M0 << l;
+  r.h = q.p.T / (double)r.M;
+  r.first = first;
+  r.count = count;
+  r.path_steps = count * spp;
+  r.item_paths = (uint32_t)item_paths;
+  r.n_items = (uint32_t)((count + item_paths - 1) / item_paths);
+  r.item_base = 0;
+  r.slot = (uint32_t)q.slot;
+  return r;
 }
 
 }  // namespace mlmc
@@ -288,26 +313,59 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
     s->models_dirty = true;
     s->active.push_back(qq.id);
   }
-  // batch: whole queries while the request table and item budget allow
+  // batch: chunks of the active queries, least pending work first (a
+  // query's key halves for every tick it waited, so none waits forever),
+  // until the tick's path-step budget, request table or item table is full
+  const uint64_t min_item = min_item_paths(s->prec, s->integ);
+  std::vector<std::pair<double, size_t>> order;
+  for (size_t k = 0; k < s->active.size(); ++k) {
+    const Query& qq = s->q[s->active[k]];
+    const double w = pending_steps(qq);
+    if (w > 0.0) order.push_back({std::ldexp(w, -std::min(qq.skipped, 1000)), k});
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+                     return a.first < b.first;
+                   });
   std::vector<PlanReq> reqs;
+  std::vector<uint64_t> req_query;
   std::vector<uint64_t> in_batch;
   uint64_t items = 0;
-  for (uint64_t id : s->active) {
-    Query& qq = s->q[id];
-    std::vector<PlanReq> mine;
-    uint64_t it = 0;
-    q_plan(qq, min_item_paths(s->prec, s->integ), mine, it);
-    if (mine.empty()) continue;
-    if (reqs.size() + mine.size() > (size_t)kMaxTableReq || items + it > (uint64_t)kMaxItems) {
-      if (reqs.empty()) return MLMC_EWORKSPACE;  // one query alone does not fit
-      continue;                                  // waits for a later tick
+  double tick_steps = 0.0;
+  bool full = false;
+  for (const auto& o : order) {
+    Query& qq = s->q[s->active[o.second]];
+    bool got = false;
+    if (!full) {
+      for (int l = qq.L; l >= qq.p.level_min && !full; --l) {
+        uint64_t next = qq.Ndone[l];
+        while (qq.dN[l] > 0) {
+          const uint64_t cp = chunk_paths(qq, l, min_item);
+          const uint64_t count = qq.dN[l] < cp ? qq.dN[l] : cp;
+          PlanReq r = chunk_request(qq, l, next, count, min_item, s->grid);
+          if (!reqs.empty() && (tick_steps + (double)r.path_steps > kTickSteps ||
+                                reqs.size() + 1 > (size_t)kMaxTableReq ||
+                                items + r.n_items > (uint64_t)kMaxItems)) {
+            full = true;
+            break;
+          }
+          r.item_base = (uint32_t)items;
+          items += r.n_items;
+          tick_steps += (double)r.path_steps;
+          reqs.push_back(r);
+          req_query.push_back(s->active[o.second]);
+          next += count;
+          qq.dN[l] -= count;
+          got = true;
+        }
+      }
     }
-    for (PlanReq& r : mine) {
-      r.item_base = (uint32_t)items;
-      items += r.n_items;
-      reqs.push_back(r);
+    if (got) {
+      qq.skipped = 0;
+      in_batch.push_back(s->active[o.second]);
+    } else {
+      qq.skipped += 1;
     }
-    in_batch.push_back(id);
   }
   if (!reqs.empty()) {
     const int n_req = (int)reqs.size();
@@ -331,24 +389,25 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
                                               cudaMemcpyDeviceToHost, st));
     if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
     if (rc) return rc;
-    // fold results into their queries (requests are grouped by query)
-    int k = 0;
+    // fold the chunks into their queries in table order (a query's chunks
+    // are contiguous and in issue order)
+    for (int k = 0; k < n_req; ++k) {
+      Query& qq = s->q[req_query[k]];
+      const PlanReq& r = s->h_reqs[k];
+      const mlmc_level_result& res = s->h_results[k];
+      const int l = r.level;
+      for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 6; ++j) qq.S[l][a][j] += res.sum[a][j];
+      qq.n[l] += res.n;
+      qq.bad[l] += res.n_nonfinite;
+      qq.steps[l] += res.path_steps;
+      qq.Ndone[l] += r.count;
+      s->path_steps += res.path_steps;
+    }
+    // advance the drivers whose pass is complete
     for (uint64_t id : in_batch) {
       Query& qq = s->q[id];
-      while (k < n_req && s->h_reqs[k].slot == (uint32_t)qq.slot) {
-        const PlanReq& r = s->h_reqs[k];
-        const mlmc_level_result& res = s->h_results[k];
-        const int l = r.level;
-        for (int a = 0; a < 2; ++a)
-          for (int j = 0; j < 6; ++j) qq.S[l][a][j] += res.sum[a][j];
-        qq.n[l] += res.n;
-        qq.bad[l] += res.n_nonfinite;
-        qq.steps[l] += res.path_steps;
-        qq.Ndone[l] += r.count;
-        qq.dN[l] = 0;
-        s->path_steps += res.path_steps;
-        ++k;
-      }
+      if (pending_steps(qq) > 0.0) continue;
       if (q_update(qq)) {
         qq.t_done = now_s();
         q_result(qq);

@@ -1,6 +1,9 @@
 """The continuous-batching query server (GPU): results are bitwise the same
 alone and in a mix of other queries, agree with the stand-alone adaptive
-estimator, and every query finishes."""
+estimator, every query finishes, a light query is not held up by heavy
+ones, and every tick keeps its path-step budget."""
+import math
+
 import pytest
 
 import paper_1612_07717_gb300 as G
@@ -50,3 +53,35 @@ def test_admission_respects_slots_and_everything_finishes():
     assert srv.stats()["finished"] == 10
     for q in ids:
         assert srv.poll(q) is not None
+
+
+def _ticks_to_finish(srv, qid, limit=10000):
+    for t in range(1, limit):
+        srv.tick()
+        if srv.poll(qid) is not None:
+            return t
+    raise AssertionError("query did not finish")
+
+
+def test_a_light_query_does_not_wait_behind_heavy_ones():
+    qs = S.draw_queries(200, seed=7)
+    rel = lambda q: round(math.log2(q[2] / q[1]["H"]))
+    heavy = [q for q in qs if rel(q) == -10 and q[1]["T"] > 3000][:3]
+    light = next(q for q in qs if rel(q) == -6)
+    alone = G.Server(max_active=8)
+    aid = alone.submit(G.make_params(light[1]), light[2])
+    t_alone = _ticks_to_finish(alone, aid)
+    srv = G.Server(max_active=8)
+    for _, d, eps in heavy:
+        srv.submit(G.make_params(d), eps)
+    lid = srv.submit(G.make_params(light[1]), light[2])
+    # the light query's passes go first and fit the tick: it needs the same ticks
+    assert _ticks_to_finish(srv, lid) <= t_alone + 1
+    assert srv.poll(lid)["estimate"] == alone.poll(aid)["estimate"]
+    # every tick stays within its path-step budget (2^28; a chunk is at most 2^26)
+    last = srv.stats()["path_steps"]
+    while srv.stats()["active"] + srv.stats()["queued"] > 0:
+        srv.tick()
+        now = srv.stats()["path_steps"]
+        assert now - last <= 2 ** 28
+        last = now
