@@ -16,6 +16,7 @@
 #pragma once
 #include "mlmc_device.cuh"
 
+
 namespace mlmc {
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -30,19 +31,21 @@ __device__ __forceinline__ float2 sel2(bool px, bool py, float2 a, float2 b) {
 // Loop constants of a level as lane pairs (kept in registers across steps).
 struct LevelX2 {
   float2 h, h2, hc, hc2;
-  float2 hl2, nhl2, hcl2, nhcl2;  // h log2 e and its negation (fine and coarse)
+  float2 hl2, hcl2;               // h log2 e (fine and coarse)
   float2 h2x, hc2x;               // -2h and -4h: the SE noise variance factor of each step
 };
 
 __device__ __forceinline__ LevelX2 make_level_x2(const Level<float>& lv) {
   LevelX2 k;
   k.h = f2(lv.h); k.h2 = f2(lv.h2); k.hc = f2(lv.hc); k.hc2 = f2(lv.hc2);
-  k.hl2 = f2(lv.hl2); k.nhl2 = f2(-lv.hl2); k.hcl2 = f2(lv.hcl2); k.nhcl2 = f2(-lv.hcl2);
+  k.hl2 = f2(lv.hl2); k.hcl2 = f2(lv.hcl2);
   k.h2x = f2(-(2.0f * lv.h)); k.hc2x = f2(-(2.0f * lv.hc));
   return k;
 }
 
-// Profiles of mlmc_device.cuh's profile(), both lanes; returns -lambda.
+// Profiles of mlmc_device.cuh's profile(), both lanes; returns -lambda (and
+// -sigma_u when NSU).
+template <bool NSU = false>
 __device__ __forceinline__ void profile_x2(const Model<float>& m, float2 z, float2& sig_u,
                                            float2& nlam, float2& g0, float2& g1) {
   const float2 zc = make_float2(fminf(fmaxf(z.x, m.eps), m.Hme), fminf(fmaxf(z.y, m.eps), m.Hme));
@@ -51,7 +54,7 @@ __device__ __forceinline__ void profile_x2(const Model<float>& m, float2 z, floa
   const float2 t = rsqrt2(s);
   const float2 q = mul2(s, t);
   const float2 s34 = mul2(q, rsqrt2(t));
-  sig_u = mul2(f2(m.A), s34);
+  sig_u = mul2(f2(NSU ? -m.A : m.A), s34);
   const float2 rz = make_float2(ptx_rcp(zc.x), ptx_rcp(zc.y));
   nlam = mul2(mul2(f2(-m.Akt), s34), add2(rz, f2(m.cfu)));
   g0 = mul2(sel2(ix, iy, f2(m.hD), f2(m.hD_out)), q);
@@ -68,11 +71,14 @@ __device__ __forceinline__ void drift_coef_x2(const Model<float>& m, float2 z, f
   g1 = mul2(sel2(ix, iy, f2(m.hDs), f2(m.hDs_out)), mul2(t, t));
 }
 
-// O-step factors (ou_factors / exp_pair of mlmc_device.cuh) from -lambda:
-// y = lambda h log2 e = nlam (-h log2 e), ny = -y = nlam (h log2 e).
-__device__ __forceinline__ void ou_factors_x2(float2 su, float2 nlam, float2 hl2, float2 nhl2,
-                                              float2& e, float2& c) {
-  const float2 y = mul2(nlam, nhl2);
+// O-step factors (ou_factors / exp_pair of mlmc_device.cuh) from -lambda,
+// with the signs carried instead of applied (a packed operand cannot be
+// negated for free): ny = nlam (h log2 e) = -y, nsu = -sigma_u and
+// nom = -(1 - e^2), from nseries = s ny and ndirect = e e - 1.  Round to
+// nearest is symmetric, so c = nsu (nom rsqrt(-nom)) has exactly the bits of
+// su (om rsqrt(om)), and ny > -0.07 is the test y < 0.07.
+__device__ __forceinline__ void ou_factors_x2(float2 nsu, float2 nlam, float2 hl2, float2& e,
+                                              float2& c) {
   const float2 ny = mul2(nlam, hl2);
   e = make_float2(ptx_ex2(ny.x), ptx_ex2(ny.y));
   const float a = 2.0f * kLn2;
@@ -81,10 +87,10 @@ __device__ __forceinline__ void ou_factors_x2(float2 su, float2 nlam, float2 hl2
   s = fma2(s, ny, f2(a * a * a / 6.0f));
   s = fma2(s, ny, f2(a * a / 2.0f));
   s = fma2(s, ny, f2(a));
-  const float2 series = mul2(s, y);
-  const float2 direct = fma2(mul2(e, f2(-1.0f)), e, f2(1.0f));
-  const float2 om = sel2(y.x < 0.07f, y.y < 0.07f, series, direct);
-  c = mul2(su, mul2(om, rsqrt2(om)));
+  const float2 nseries = mul2(s, ny);
+  const float2 ndirect = fma2(e, e, f2(-1.0f));
+  const float2 nom = sel2(ny.x > -0.07f, ny.y > -0.07f, nseries, ndirect);
+  c = mul2(nsu, mul2(nom, make_float2(ptx_rsqrt(-nom.x), ptx_rsqrt(-nom.y))));
 }
 
 // Box-Muller of mlmc_device.cuh on two word pairs (lane x: path a, lane y:
@@ -141,10 +147,10 @@ __device__ __forceinline__ void se_step_x2(const Model<float>& m, float2 h, floa
 }
 
 __device__ __forceinline__ float2 gl_step_x2(const Model<float>& m, float2 h, float2 hl2,
-                                             float2 nhl2, PathX2& p, float2 xi) {
-  float2 su, nlam, g0, g1, e, c;
-  profile_x2(m, p.z, su, nlam, g0, g1);
-  ou_factors_x2(su, nlam, hl2, nhl2, e, c);
+                                             PathX2& p, float2 xi) {
+  float2 nsu, nlam, g0, g1, e, c;
+  profile_x2<true>(m, p.z, nsu, nlam, g0, g1);
+  ou_factors_x2(nsu, nlam, hl2, e, c);
   const float2 us = fma2(c, xi, mul2(e, p.w));
   p.w = fma2(h, fma2(mul2(g1, us), us, g0), us);
   track_wm(p);
@@ -160,11 +166,11 @@ __device__ __forceinline__ void baoab_pre_x2(const Model<float>& m, float2 h2, P
   reflect_x2(m, p);
 }
 
-__device__ __forceinline__ float2 baoab_post_x2(const Model<float>& m, float2 hl2, float2 nhl2,
-                                                float2 h2, PathX2& p, float2 xi) {
-  float2 su, nlam, g0, g1, e, c;
-  profile_x2(m, p.z, su, nlam, g0, g1);
-  ou_factors_x2(su, nlam, hl2, nhl2, e, c);
+__device__ __forceinline__ float2 baoab_post_x2(const Model<float>& m, float2 hl2, float2 h2,
+                                                PathX2& p, float2 xi) {
+  float2 nsu, nlam, g0, g1, e, c;
+  profile_x2<true>(m, p.z, nsu, nlam, g0, g1);
+  ou_factors_x2(nsu, nlam, hl2, e, c);
   p.w = fma2(c, xi, mul2(e, p.w));
   track_wm(p);
   p.z = fma2(p.w, h2, p.z);
@@ -183,11 +189,11 @@ __device__ __forceinline__ void fine_step_x2(const Model<float>& m, const LevelX
     se_step_x2(m, k.h, k.h2x, p, xi);
   } else if (INTEG == kGL) {
     Sn = p.S;
-    e = gl_step_x2(m, k.h, k.hl2, k.nhl2, p, xi);
+    e = gl_step_x2(m, k.h, k.hl2, p, xi);
   } else {
     baoab_pre_x2(m, k.h2, p);
     Sn = p.S;
-    e = baoab_post_x2(m, k.hl2, k.nhl2, k.h2, p, xi);
+    e = baoab_post_x2(m, k.hl2, k.h2, p, xi);
   }
 }
 
@@ -205,13 +211,13 @@ __device__ __forceinline__ void coarse_step_x2(const Model<float>& m, const Leve
     const float2 Sc = m.coupling ? f2(1.0f) : p.S;
     const float2 xc = mul2(mul2(Sc, rsqrt2(fma2(ea, ea, f2(1.0f)))),
                            fma2(mul2(ea, Sa), xa, mul2(Sb, xb)));
-    gl_step_x2(m, k.hc, k.hcl2, k.nhcl2, p, xc);
+    gl_step_x2(m, k.hc, k.hcl2, p, xc);
   } else {
     baoab_pre_x2(m, k.hc2, p);
     const float2 Sc = m.coupling ? f2(1.0f) : p.S;
     const float2 xc = mul2(mul2(Sc, rsqrt2(fma2(ea, ea, f2(1.0f)))),
                            fma2(mul2(ea, Sa), xa, mul2(Sb, xb)));
-    baoab_post_x2(m, k.hcl2, k.nhcl2, k.hc2, p, xc);
+    baoab_post_x2(m, k.hcl2, k.hc2, p, xc);
   }
 }
 
