@@ -221,26 +221,57 @@ __device__ __forceinline__ void coarse_step_x2(const Model<float>& m, const Leve
   }
 }
 
+// What the start of every pair shares when z0 is fixed (w0 modes 0 and 1):
+// sigma_u(z0) for the initial velocity and the BAOAB drift coefficients at
+// z0.  Computed once per work item by the operations initial_state and
+// drift_coef_x2 perform for each pair, so the start values keep their bits.
+struct StartX2 {
+  float su0;
+  float2 g0, g1;
+};
+
+__device__ __forceinline__ StartX2 start_x2(const Model<float>& m) {
+  StartX2 s;
+  float lam, g0, g1;
+  profile(m, m.z0, s.su0, lam, g0, g1);
+  drift_coef_x2(m, f2(m.z0), s.g0, s.g1);
+  return s;
+}
+
 // Path pairs i and i + 1 of a level, fast reflection; flag_x / flag_y report
 // a lane that needs the exact replay (see reflect_fast).
 template <int INTEG, bool COUPLED>
 __device__ __forceinline__ void run_pair_x2_fast(const Model<float>& m, const Level<float>& lv,
-                                                 uint64_t i, PathX2& f, PathX2& c, bool& flx,
-                                                 bool& fly) {
+                                                 const StartX2& s0, uint64_t i, PathX2& f,
+                                                 PathX2& c, bool& flx, bool& fly) {
   const uint64_t i1 = i + 1;
   const uint32_t alo = (uint32_t)i, ahi = (uint32_t)(i >> 32);
   const uint32_t blo = (uint32_t)i1, bhi = (uint32_t)(i1 >> 32);
   const uint32_t aw2 = ahi ^ lv.c2, bw2 = bhi ^ lv.c2;
-  float za, wa, zb, wb;
-  initial_state(m, lv, alo, ahi, za, wa);
-  initial_state(m, lv, blo, bhi, zb, wb);
-  f.z = make_float2(za, zb);
-  f.w = make_float2(wa, wb);
   f.S = f2(1.0f);
   f.g0 = f2(0.0f);
   f.g1 = f2(0.0f);
   f.wm = f2(0.0f);
-  if (INTEG == kBAOAB) drift_coef_x2(m, f.z, f.g0, f.g1);
+  if (m.w0_mode == 2) {  // well mixed: each pair draws its own height
+    float za, wa, zb, wb;
+    initial_state(m, lv, alo, ahi, za, wa);
+    initial_state(m, lv, blo, bhi, zb, wb);
+    f.z = make_float2(za, zb);
+    f.w = make_float2(wa, wb);
+    if (INTEG == kBAOAB) drift_coef_x2(m, f.z, f.g0, f.g1);
+  } else {
+    f.z = f2(m.z0);
+    f.w = f2(m.w0);
+    if (m.w0_mode == 1) {  // initial_state's draw from the reserved block
+      const uint4 xa = philox10(m.rk0, m.rk1, 0xFFFFFFFFu, alo, aw2, m.stream_id);
+      const uint4 xb = philox10(m.rk0, m.rk1, 0xFFFFFFFFu, blo, bw2, m.stream_id);
+      float na, nb, unused;
+      box_muller(xa.x, xa.y, na, unused);
+      box_muller(xb.x, xb.y, nb, unused);
+      f.w = make_float2(s0.su0 * na, s0.su0 * nb);
+    }
+    if (INTEG == kBAOAB) { f.g0 = s0.g0; f.g1 = s0.g1; }
+  }
   c = f;
   const LevelX2 k = make_level_x2(lv);
   const int64_t M = lv.M;

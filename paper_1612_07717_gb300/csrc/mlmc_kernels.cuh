@@ -285,10 +285,11 @@ __device__ __forceinline__ void finish_lane(const Model<float>& m, const Level<f
 template <int INTEG, bool COUPLED>
 __device__ __forceinline__ void multilevel_item_x2(const Model<float>& m, const Level<float>& lv,
                                                    uint64_t first, uint32_t count, Acc& acc) {
+  const StartX2 s0 = start_x2(m);
   for (uint32_t j = 2 * threadIdx.x; j < count; j += 2 * kBlock) {
     PathX2 f, c;
     bool mx, my;
-    run_pair_x2_fast<INTEG, COUPLED>(m, lv, first + j, f, c, mx, my);
+    run_pair_x2_fast<INTEG, COUPLED>(m, lv, s0, first + j, f, c, mx, my);
     finish_lane<INTEG, COUPLED>(m, lv, first + j, f.z.x, f.w.x, c.z.x, c.w.x, mx, acc);
     if (j + 1 < count)
       finish_lane<INTEG, COUPLED>(m, lv, first + j + 1, f.z.y, f.w.y, c.z.y, c.w.y, my, acc);
