@@ -85,3 +85,29 @@ def test_a_light_query_does_not_wait_behind_heavy_ones():
         now = srv.stats()["path_steps"]
         assert now - last <= 2 ** 28
         last = now
+
+
+def test_sampled_queries_match_the_fp64_oracle():
+    """Per-query error of served estimates against the FP64 CPU oracle on a
+    sampled subset of the serving stream: every 10th of its first 200
+    queries whose tolerance the oracle can afford (eps/H = 2^-6 and 2^-8;
+    the 2^-10 queries would need about 1e9 oracle path-steps each).  The
+    reference is the oracle's own MLMC estimate at eps/4 with an independent
+    seed, so (estimate - reference)^2 / eps^2 has mean at most about
+    1 + 1/16 when each estimate meets its RMSE target."""
+    from oracle import oracle as O
+    from parity import oracle_params
+    qs = S.draw_queries(200, seed=7)
+    served = _drain(G.Server(max_active=32), qs)
+    ratios = []
+    for k in range(0, 200, 10):
+        _, d, eps = qs[k]
+        if round(math.log2(eps / d["H"])) == -10:
+            continue
+        ref = O.estimate(oracle_params(d, G.FP64), G.BAOAB, eps / 4, seed=1000 + k)
+        ratios.append(((served[k]["estimate"][0] - ref["estimate"][0]) / eps) ** 2)
+    rmse_over_eps = math.sqrt(sum(ratios) / len(ratios))
+    print("\nserved estimates against the FP64 oracle: %d queries, RMSE / eps = %.3f"
+          % (len(ratios), rmse_over_eps))
+    assert len(ratios) >= 10
+    assert rmse_over_eps <= 1.25, ratios
