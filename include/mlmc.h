@@ -339,23 +339,30 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  * estimate (the rule of mlmc_estimate) of its own scenario and tolerance;
  * its Philox stream is p->stream_id, the key is the server's seed.
  *   mlmc_server_workspace_bytes  device workspace for max_active queries
- *                                (model slots, request table, partials)
- *   mlmc_server_create   binds the workspace and stream; allocates only
- *                        pinned host staging buffers
+ *                                (model slots; the request table, results
+ *                                and partials of each launch in flight)
+ *   mlmc_server_create   binds the workspace; work queued on `stream`
+ *                        before the call is ordered before the server's
+ *                        launches, which run on four streams of its own;
+ *                        allocates those streams, their events and pinned
+ *                        host staging buffers (no device memory)
  *   mlmc_server_submit   validates and queues a query; returns its id
- *   mlmc_server_tick     admits queued queries while a slot is free, runs
- *                        ONE persistent launch over chunks (at most 2^26
- *                        path-steps each) of the active queries' pending
- *                        passes -- least pending work first, a waiting
- *                        query's priority doubling every tick -- up to
- *                        2^28 path-steps, 2048 requests and 32768 work
- *                        items per tick (always at least one chunk);
- *                        reduces each chunk in item order, folds chunks
- *                        into their queries in chunk order, advances the
- *                        driver of every query whose pass is complete and
- *                        retires finished queries; synchronises the stream.
- *                        n_done: queries finished in this tick; n_active:
- *                        queries left (active and queued)
+ *   mlmc_server_tick     folds the launches that have completed (oldest
+ *                        first), admits queued queries while a slot is
+ *                        free, and puts one more launch in flight (at most
+ *                        four): one persistent launch over chunks (at most
+ *                        2^26 path-steps each) of the active queries'
+ *                        pending passes -- least pending work first, a
+ *                        waiting query's priority doubling every launch --
+ *                        up to 2^28 path-steps, 2048 requests and 32768
+ *                        work items, holding only pairs at most 4 times as
+ *                        long as its first chunk's (or 2048 path-steps);
+ *                        when all four are in flight, or nothing is left
+ *                        to issue, it first waits for the oldest.  A folded
+ *                        chunk enters its query in chunk order; a query
+ *                        whose pass is folded advances its driver and may
+ *                        finish.  n_done: queries finished in this call;
+ *                        n_active: queries left (active and queued)
  *   mlmc_server_poll     1 while the query runs; its final status (MLMC_OK,
  *                        MLMC_ENOTCONV, MLMC_ENONFINITE) with the result and
  *                        its submit-to-finish latency once done
@@ -364,8 +371,8 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  *                        active, queued}
  * A pass's chunks, their split into work items and their folding order
  * depend only on the query (and the server's grid), so a query's result is
- * bitwise the same alone and in any mix; the budget decides only when a
- * chunk runs. */
+ * bitwise the same alone and in any mix; the scheduling decides only when a
+ * chunk runs.  mlmc_server_destroy waits for the launches in flight. */
 typedef struct mlmc_server_s* mlmc_server;
 size_t mlmc_server_workspace_bytes(int max_active);
 int mlmc_server_create(int integrator, int precision, int max_active, uint64_t seed,

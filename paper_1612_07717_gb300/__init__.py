@@ -457,9 +457,10 @@ class Server:
     """Continuous-batching server of dispersion queries (``mlmc_server_*``).
 
     ``submit`` queues a query (a ``Params`` with its own scenario and
-    ``stream_id``) with its tolerance; ``tick`` runs one batched launch over
-    every active query and retires the finished ones; ``poll`` returns a
-    finished query's result and latency.
+    ``stream_id``) with its tolerance; ``tick`` folds the completed launches,
+    retires the finished queries and puts one more batched launch in flight
+    (up to four at once); ``poll`` returns a finished query's result and
+    latency.
     """
 
     def __init__(self, integrator=BAOAB, precision=FP32, max_active=64, seed=1, stream=None):

@@ -5,20 +5,23 @@
 // A query holds a device slot (its Model) while active.  A pass of a query's
 // driver (the n_init samples of a new level, or the extra samples its
 // variance estimate asks for) is cut into chunks of at most kChunkSteps
-// path-steps; every tick the server fills ONE request table with chunks of
-// the active queries -- the query with the least work left in its pass
-// first, up to kTickSteps path-steps in all -- runs one persistent
-// multi-level launch over it, reduces each chunk in item order, folds the
-// chunks into their queries in chunk order, and advances a query's driver
-// once its pass is complete.  Finished queries release their slot and queued
-// queries are admitted in arrival order while a slot is free.  Light queries
-// therefore do not wait behind a heavy query's whole pass, and a tick stays
-// short however many heavy queries are active.
+// path-steps.  A launch is one persistent multi-level kernel over a request
+// table of chunks -- the query with the least work left in its pass first,
+// up to kTickSteps path-steps, and only pairs at most kChainRatio times as
+// long as the first chunk's (a launch lasts as long as its longest pair) --
+// followed by the per-chunk reduction in item order.  Up to kInFlight
+// launches run at once, each on its own stream; they are folded in issue
+// order, each chunk into its query in chunk order, and a query's driver
+// advances once every chunk of its pass is folded.  Finished queries release
+// their slot; queued queries take free slots in arrival order.  So a light
+// query neither waits for a heavy query's whole pass nor shares a launch
+// with its long pairs, and the GPU keeps working on other launches while one
+// waits for its longest pair.
 //
 // The chunks of a pass, a chunk's split into work items and the order in
 // which chunks are folded depend only on the query (and the server's grid),
 // never on what else is active, so a query's sums -- and its estimate -- are
-// bitwise the same alone and among other queries; the tick budget decides
+// bitwise the same alone and among other queries; the scheduling decides
 // only WHEN a chunk runs.
 #include <algorithm>
 #include <chrono>
@@ -36,7 +39,10 @@ constexpr int kMaxTableReq = 2048;          // requests per tick
 constexpr double kItemTarget = 1 << 20;     // largest work item, path-steps
 constexpr uint64_t kMaxItemsPerReq = 1024;  // items one request may use
 constexpr double kChunkSteps = 1 << 26;     // path-steps of one chunk (one request)
-constexpr double kTickSteps = 1 << 28;      // path-steps of one tick (at least one chunk)
+constexpr double kTickSteps = 1 << 28;      // path-steps of one launch (at least one chunk)
+constexpr int kInFlight = 4;                // launches in flight at once
+constexpr double kChainRatio = 4.0;         // longest / first pair length in one launch
+constexpr double kChainFloor = 2048.0;      // path-steps per pair any launch may hold
 constexpr size_t kModelSlot = 512;          // bytes reserved per Model
 constexpr int kQLevels = MLMC_MAX_LEVELS;
 
@@ -48,9 +54,11 @@ struct Query {
   int slot = -1;
   int state = 0;  // 0 queued, 1 active, 2 done
   int L = 0, pass = 0, converged = 0;
-  // Ndone: samples folded; dN: samples of the current pass not yet issued
-  uint64_t Ndone[kQLevels] = {0}, dN[kQLevels] = {0};
-  int skipped = 0;  // ticks in a row this query waited with work pending
+  // Ndone: samples folded; Nnext: next sample to issue; dN: samples of the
+  // current pass not yet issued
+  uint64_t Ndone[kQLevels] = {0}, Nnext[kQLevels] = {0}, dN[kQLevels] = {0};
+  int inflight = 0;  // chunks issued and not yet folded
+  int skipped = 0;   // launches in a row this query waited with work pending
   uint64_t n[kQLevels] = {0}, bad[kQLevels] = {0}, steps[kQLevels] = {0};
   double S[kQLevels][2][6] = {};
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -182,35 +190,230 @@ static PlanReq chunk_request(const Query& q, int l, uint64_t first, uint64_t cou
 
 using namespace mlmc;
 
-struct mlmc_server_s {
-  int integ = 0, prec = 0, max_active = 0, grid = 0;
-  uint64_t seed = 0;
+// One launch in flight: its own stream, request table, partials, results
+// and completion event.  Launches complete and are folded in issue order.
+struct Flight {
   cudaStream_t st = nullptr;
-  // device memory, carved from the caller's workspace
+  cudaEvent_t done = nullptr;
   unsigned int* d_counter = nullptr;
-  char* d_models = nullptr;
   PlanReq* d_reqs = nullptr;
   mlmc_level_result* d_results = nullptr;
   Partial* d_partials = nullptr;
-  // pinned host staging
-  char* h_models = nullptr;
-  PlanReq* h_reqs = nullptr;
-  mlmc_level_result* h_results = nullptr;
-  bool models_dirty = false;
+  PlanReq* h_reqs = nullptr;                 // pinned
+  mlmc_level_result* h_results = nullptr;    // pinned
+  std::vector<uint64_t> req_query;           // the query of each request
+  int n_req = 0;
+};
+
+struct mlmc_server_s {
+  int integ = 0, prec = 0, max_active = 0, grid = 0;
+  uint64_t seed = 0;
+  char* d_models = nullptr;                  // carved from the caller's workspace
+  char* h_models = nullptr;                  // pinned staging of the Model slots
+  cudaStream_t up_st = nullptr;              // Model uploads
+  cudaEvent_t up_ev = nullptr;               // after the latest upload
+  Flight fl[kInFlight];
+  std::deque<int> busy;                      // flights in flight, oldest first
+  std::vector<int> idle;
   uint64_t next_id = 1;
   std::unordered_map<uint64_t, Query> q;
   std::deque<uint64_t> queue;
-  std::vector<uint64_t> active;   // admission order
+  std::vector<uint64_t> active;              // admission order
+  std::vector<uint64_t> to_upload;           // admitted, Model not yet on the device
   std::vector<int> free_slots;
-  std::vector<uint64_t> done_order;
   // statistics
   uint64_t ticks = 0, path_steps = 0, completed = 0;
   double busy_s = 0.0;
 };
 
-static size_t server_bytes(int max_active) {
-  return 256 + (size_t)max_active * kModelSlot + (size_t)kMaxTableReq * sizeof(PlanReq) +
+static size_t flight_bytes() {
+  return 256 + (size_t)kMaxTableReq * sizeof(PlanReq) +
          (size_t)kMaxTableReq * sizeof(mlmc_level_result) + (size_t)kMaxItems * sizeof(Partial);
+}
+
+static size_t server_bytes(int max_active) {
+  return (size_t)max_active * kModelSlot + (size_t)kInFlight * flight_bytes();
+}
+
+static void server_free(mlmc_server_s* s) {
+  for (Flight& f : s->fl) {
+    if (f.st) cudaStreamSynchronize(f.st);
+    if (f.done) cudaEventDestroy(f.done);
+    if (f.st) cudaStreamDestroy(f.st);
+    if (f.h_reqs) cudaFreeHost(f.h_reqs);
+    if (f.h_results) cudaFreeHost(f.h_results);
+  }
+  if (s->up_st) cudaStreamSynchronize(s->up_st);
+  if (s->up_ev) cudaEventDestroy(s->up_ev);
+  if (s->up_st) cudaStreamDestroy(s->up_st);
+  if (s->h_models) cudaFreeHost(s->h_models);
+  delete s;
+}
+
+// Retire a finished query: result, statistics, its slot back to the pool.
+static void retire(mlmc_server_s* s, Query& qq, int* done) {
+  qq.t_done = now_s();
+  q_result(qq);
+  qq.state = 2;
+  s->free_slots.push_back(qq.slot);
+  qq.slot = -1;
+  ++*done;
+  ++s->completed;
+}
+
+// Fold the oldest flight (waiting for it when `wait`); false when there is
+// none or it has not completed.  Its chunks enter their queries in table
+// order, which is each query's chunk order; a query whose pass is then
+// complete advances its driver and may finish.
+static int fold_oldest(mlmc_server_s* s, bool wait, bool* folded, int* done) {
+  *folded = false;
+  if (s->busy.empty()) return MLMC_OK;
+  Flight& f = s->fl[s->busy.front()];
+  if (wait) {
+    int rc = cuda_status(cudaEventSynchronize(f.done));
+    if (rc) return rc;
+  } else {
+    const cudaError_t e = cudaEventQuery(f.done);
+    if (e == cudaErrorNotReady) return MLMC_OK;
+    if (e != cudaSuccess) return MLMC_ECUDA;
+  }
+  std::vector<uint64_t> touched;
+  for (int k = 0; k < f.n_req; ++k) {
+    Query& qq = s->q[f.req_query[k]];
+    const PlanReq& r = f.h_reqs[k];
+    const mlmc_level_result& res = f.h_results[k];
+    const int l = r.level;
+    for (int a = 0; a < 2; ++a)
+      for (int j = 0; j < 6; ++j) qq.S[l][a][j] += res.sum[a][j];
+    qq.n[l] += res.n;
+    qq.bad[l] += res.n_nonfinite;
+    qq.steps[l] += res.path_steps;
+    qq.Ndone[l] += r.count;
+    qq.inflight -= 1;
+    s->path_steps += res.path_steps;
+    if (touched.empty() || touched.back() != f.req_query[k]) touched.push_back(f.req_query[k]);
+  }
+  for (uint64_t id : touched) {
+    Query& qq = s->q[id];
+    if (qq.state != 1 || qq.inflight || pending_steps(qq) > 0.0) continue;
+    if (q_update(qq)) retire(s, qq, done);
+  }
+  std::vector<uint64_t> still;
+  for (uint64_t id : s->active)
+    if (s->q[id].state == 1) still.push_back(id);
+  s->active.swap(still);
+  s->idle.push_back(s->busy.front());
+  s->busy.pop_front();
+  *folded = true;
+  return MLMC_OK;
+}
+
+// Queued queries take free slots in arrival order.
+static void admit(mlmc_server_s* s) {
+  while (!s->queue.empty() && !s->free_slots.empty()) {
+    Query& qq = s->q[s->queue.front()];
+    s->queue.pop_front();
+    qq.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    qq.state = 1;
+    qq.t_admit = now_s();
+    qq.L = qq.p.level_min;
+    qq.pass = 0;
+    qq.dN[qq.L] = (uint64_t)qq.p.n_init;
+    model_image(s->prec, qq.hm, s->h_models + (size_t)qq.slot * kModelSlot);
+    s->to_upload.push_back(qq.id);
+    s->active.push_back(qq.id);
+  }
+}
+
+// Fill an idle flight with chunks -- least pending work first (a query's
+// key halves for every launch it waited), up to the path-step budget, the
+// request table and the item table -- and launch it.  *launched is false
+// when no query has work to issue.
+static int issue(mlmc_server_s* s, bool* launched) {
+  *launched = false;
+  if (s->idle.empty()) return MLMC_OK;
+  const uint64_t min_item = min_item_paths(s->prec, s->integ);
+  std::vector<std::pair<double, size_t>> order;
+  for (size_t k = 0; k < s->active.size(); ++k) {
+    const Query& qq = s->q[s->active[k]];
+    const double w = pending_steps(qq);
+    if (w > 0.0) order.push_back({std::ldexp(w, -std::min(qq.skipped, 1000)), k});
+  }
+  if (order.empty()) return MLMC_OK;
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+                     return a.first < b.first;
+                   });
+  const int fi = s->idle.back();
+  Flight& f = s->fl[fi];
+  f.req_query.clear();
+  int n_req = 0;
+  uint64_t items = 0;
+  double steps = 0.0, chain_cap = 0.0;
+  bool full = false;
+  for (const auto& o : order) {
+    Query& qq = s->q[s->active[o.second]];
+    bool got = false;
+    for (int l = qq.L; l >= qq.p.level_min && !full; --l) {
+      // a launch lasts at least as long as its longest pair: keep pairs of
+      // very different length apart, so short pairs are not held up
+      const double spp = (double)q_steps(qq, l);
+      if (n_req == 0) chain_cap = std::max(kChainRatio * spp, kChainFloor);
+      if (spp > chain_cap) continue;
+      while (qq.dN[l] > 0) {
+        const uint64_t cp = chunk_paths(qq, l, min_item);
+        const uint64_t count = qq.dN[l] < cp ? qq.dN[l] : cp;
+        PlanReq r = chunk_request(qq, l, qq.Nnext[l], count, min_item, s->grid);
+        if (n_req > 0 && (steps + (double)r.path_steps > kTickSteps || n_req + 1 > kMaxTableReq ||
+                          items + r.n_items > (uint64_t)kMaxItems)) {
+          full = true;
+          break;
+        }
+        r.item_base = (uint32_t)items;
+        items += r.n_items;
+        steps += (double)r.path_steps;
+        f.h_reqs[n_req++] = r;
+        f.req_query.push_back(qq.id);
+        qq.Nnext[l] += count;
+        qq.dN[l] -= count;
+        qq.inflight += 1;
+        got = true;
+      }
+    }
+    qq.skipped = got ? 0 : qq.skipped + 1;
+  }
+  f.n_req = n_req;
+  s->idle.pop_back();
+  s->busy.push_back(fi);
+  int rc = MLMC_OK;
+  // Models of newly admitted queries go up on their own stream; every
+  // launch waits for the latest upload.
+  if (!s->to_upload.empty()) {
+    for (uint64_t id : s->to_upload) {
+      const Query& qq = s->q[id];
+      if (qq.state != 1) continue;
+      const size_t off = (size_t)qq.slot * kModelSlot;
+      if (!rc) rc = cuda_status(cudaMemcpyAsync(s->d_models + off, s->h_models + off, kModelSlot,
+                                                cudaMemcpyHostToDevice, s->up_st));
+    }
+    s->to_upload.clear();
+    if (!rc) rc = cuda_status(cudaEventRecord(s->up_ev, s->up_st));
+  }
+  if (!rc) rc = cuda_status(cudaStreamWaitEvent(f.st, s->up_ev, 0));
+  if (!rc) rc = cuda_status(cudaMemcpyAsync(f.d_reqs, f.h_reqs, n_req * sizeof(PlanReq),
+                                            cudaMemcpyHostToDevice, f.st));
+  if (!rc) rc = cuda_status(cudaMemsetAsync(f.d_counter, 0, sizeof(unsigned int), f.st));
+  if (!rc) rc = cuda_status(launch_multilevel_table(s->prec, s->integ, s->d_models, kModelSlot,
+                                                    f.d_reqs, n_req, (uint32_t)items, f.d_partials,
+                                                    f.d_counter, s->grid, f.st));
+  if (!rc) rc = cuda_status(launch_finalize_table(f.d_partials, f.d_reqs, n_req, f.d_results, f.st));
+  if (!rc) rc = cuda_status(cudaMemcpyAsync(f.h_results, f.d_results,
+                                            n_req * sizeof(mlmc_level_result),
+                                            cudaMemcpyDeviceToHost, f.st));
+  if (!rc) rc = cuda_status(cudaEventRecord(f.done, f.st));
+  *launched = rc == MLMC_OK;
+  return rc;
 }
 
 extern "C" {
@@ -238,27 +441,42 @@ int mlmc_server_create(int integrator, int precision, int max_active, uint64_t s
   s->max_active = max_active;
   s->seed = seed;
   s->grid = grid;
-  s->st = (cudaStream_t)stream;
   char* b = (char*)workspace;
-  s->d_counter = (unsigned int*)b;
-  b += 256;
   s->d_models = b;
   b += (size_t)max_active * kModelSlot;
-  s->d_reqs = (PlanReq*)b;
-  b += (size_t)kMaxTableReq * sizeof(PlanReq);
-  s->d_results = (mlmc_level_result*)b;
-  b += (size_t)kMaxTableReq * sizeof(mlmc_level_result);
-  s->d_partials = (Partial*)b;
-  if (cudaHostAlloc((void**)&s->h_models, (size_t)max_active * kModelSlot, cudaHostAllocDefault) !=
-          cudaSuccess ||
-      cudaHostAlloc((void**)&s->h_reqs, kMaxTableReq * sizeof(PlanReq), cudaHostAllocDefault) !=
-          cudaSuccess ||
-      cudaHostAlloc((void**)&s->h_results, kMaxTableReq * sizeof(mlmc_level_result),
-                    cudaHostAllocDefault) != cudaSuccess) {
-    if (s->h_models) cudaFreeHost(s->h_models);
-    if (s->h_reqs) cudaFreeHost(s->h_reqs);
-    if (s->h_results) cudaFreeHost(s->h_results);
-    delete s;
+  bool ok = cudaHostAlloc((void**)&s->h_models, (size_t)max_active * kModelSlot,
+                          cudaHostAllocDefault) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->up_st, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->up_ev, cudaEventDisableTiming) == cudaSuccess;
+  // work the caller queued on its stream (e.g. clearing the workspace)
+  // comes before anything the server launches
+  cudaEvent_t start = nullptr;
+  ok = ok && cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventRecord(start, (cudaStream_t)stream) == cudaSuccess &&
+       cudaStreamWaitEvent(s->up_st, start, 0) == cudaSuccess &&
+       cudaEventRecord(s->up_ev, s->up_st) == cudaSuccess;
+  for (int k = 0; k < kInFlight && ok; ++k) {
+    Flight& f = s->fl[k];
+    f.d_counter = (unsigned int*)b;
+    b += 256;
+    f.d_reqs = (PlanReq*)b;
+    b += (size_t)kMaxTableReq * sizeof(PlanReq);
+    f.d_results = (mlmc_level_result*)b;
+    b += (size_t)kMaxTableReq * sizeof(mlmc_level_result);
+    f.d_partials = (Partial*)b;
+    b += (size_t)kMaxItems * sizeof(Partial);
+    ok = cudaStreamCreateWithFlags(&f.st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaHostAlloc((void**)&f.h_reqs, kMaxTableReq * sizeof(PlanReq), cudaHostAllocDefault) ==
+             cudaSuccess &&
+         cudaHostAlloc((void**)&f.h_results, kMaxTableReq * sizeof(mlmc_level_result),
+                       cudaHostAllocDefault) == cudaSuccess &&
+         cudaStreamWaitEvent(f.st, start, 0) == cudaSuccess;
+    s->idle.push_back(kInFlight - 1 - k);
+  }
+  if (start) cudaEventDestroy(start);
+  if (!ok) {
+    server_free(s);
     return MLMC_ECUDA;
   }
   std::memset(s->h_models, 0, (size_t)max_active * kModelSlot);
@@ -293,137 +511,32 @@ int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t
   return MLMC_OK;
 }
 
-// One scheduling tick: admit, batch, launch, reduce, advance the drivers.
+// One scheduling step: fold the completed launches, admit, and put one more
+// launch in flight; when every flight is busy, or there is nothing new to
+// issue, wait for the oldest launch first.  Each call folds or launches at
+// least once while any query is active.
 int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
   if (!s) return MLMC_EINVAL;
   const double t0 = now_s();
-  int done = 0;
-  // admission: a free slot per query, in arrival order
-  while (!s->queue.empty() && !s->free_slots.empty()) {
-    Query& qq = s->q[s->queue.front()];
-    s->queue.pop_front();
-    qq.slot = s->free_slots.back();
-    s->free_slots.pop_back();
-    qq.state = 1;
-    qq.t_admit = now_s();
-    qq.L = qq.p.level_min;
-    qq.pass = 0;
-    qq.dN[qq.L] = (uint64_t)qq.p.n_init;
-    model_image(s->prec, qq.hm, s->h_models + (size_t)qq.slot * kModelSlot);
-    s->models_dirty = true;
-    s->active.push_back(qq.id);
-  }
-  // batch: chunks of the active queries, least pending work first (a
-  // query's key halves for every tick it waited, so none waits forever),
-  // until the tick's path-step budget, request table or item table is full
-  const uint64_t min_item = min_item_paths(s->prec, s->integ);
-  std::vector<std::pair<double, size_t>> order;
-  for (size_t k = 0; k < s->active.size(); ++k) {
-    const Query& qq = s->q[s->active[k]];
-    const double w = pending_steps(qq);
-    if (w > 0.0) order.push_back({std::ldexp(w, -std::min(qq.skipped, 1000)), k});
-  }
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
-                     return a.first < b.first;
-                   });
-  std::vector<PlanReq> reqs;
-  std::vector<uint64_t> req_query;
-  std::vector<uint64_t> in_batch;
-  uint64_t items = 0;
-  double tick_steps = 0.0;
-  bool full = false;
-  for (const auto& o : order) {
-    Query& qq = s->q[s->active[o.second]];
-    bool got = false;
-    if (!full) {
-      for (int l = qq.L; l >= qq.p.level_min && !full; --l) {
-        uint64_t next = qq.Ndone[l];
-        while (qq.dN[l] > 0) {
-          const uint64_t cp = chunk_paths(qq, l, min_item);
-          const uint64_t count = qq.dN[l] < cp ? qq.dN[l] : cp;
-          PlanReq r = chunk_request(qq, l, next, count, min_item, s->grid);
-          if (!reqs.empty() && (tick_steps + (double)r.path_steps > kTickSteps ||
-                                reqs.size() + 1 > (size_t)kMaxTableReq ||
-                                items + r.n_items > (uint64_t)kMaxItems)) {
-            full = true;
-            break;
-          }
-          r.item_base = (uint32_t)items;
-          items += r.n_items;
-          tick_steps += (double)r.path_steps;
-          reqs.push_back(r);
-          req_query.push_back(s->active[o.second]);
-          next += count;
-          qq.dN[l] -= count;
-          got = true;
-        }
-      }
-    }
-    if (got) {
-      qq.skipped = 0;
-      in_batch.push_back(s->active[o.second]);
-    } else {
-      qq.skipped += 1;
+  int done = 0, rc = MLMC_OK;
+  bool folded = true, launched = false;
+  while (!rc && folded) rc = fold_oldest(s, false, &folded, &done);
+  if (!rc) {
+    admit(s);
+    if (s->idle.empty()) {
+      rc = fold_oldest(s, true, &folded, &done);
+      if (!rc) admit(s);
     }
   }
-  if (!reqs.empty()) {
-    const int n_req = (int)reqs.size();
-    std::memcpy(s->h_reqs, reqs.data(), n_req * sizeof(PlanReq));
-    cudaStream_t st = s->st;
-    int rc = MLMC_OK;
-    if (s->models_dirty) {
-      rc = cuda_status(cudaMemcpyAsync(s->d_models, s->h_models, (size_t)s->max_active * kModelSlot,
-                                       cudaMemcpyHostToDevice, st));
-      s->models_dirty = false;
+  if (!rc) rc = issue(s, &launched);
+  if (!rc && !launched && !s->busy.empty()) {
+    rc = fold_oldest(s, true, &folded, &done);
+    if (!rc) {
+      admit(s);
+      rc = issue(s, &launched);
     }
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->d_reqs, s->h_reqs, n_req * sizeof(PlanReq),
-                                              cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_status(cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned int), st));
-    if (!rc) rc = cuda_status(launch_multilevel_table(s->prec, s->integ, s->d_models, kModelSlot,
-                                                      s->d_reqs, n_req, (uint32_t)items,
-                                                      s->d_partials, s->d_counter, s->grid, st));
-    if (!rc) rc = cuda_status(launch_finalize_table(s->d_partials, s->d_reqs, n_req, s->d_results, st));
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->h_results, s->d_results,
-                                              n_req * sizeof(mlmc_level_result),
-                                              cudaMemcpyDeviceToHost, st));
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
-    if (rc) return rc;
-    // fold the chunks into their queries in table order (a query's chunks
-    // are contiguous and in issue order)
-    for (int k = 0; k < n_req; ++k) {
-      Query& qq = s->q[req_query[k]];
-      const PlanReq& r = s->h_reqs[k];
-      const mlmc_level_result& res = s->h_results[k];
-      const int l = r.level;
-      for (int a = 0; a < 2; ++a)
-        for (int j = 0; j < 6; ++j) qq.S[l][a][j] += res.sum[a][j];
-      qq.n[l] += res.n;
-      qq.bad[l] += res.n_nonfinite;
-      qq.steps[l] += res.path_steps;
-      qq.Ndone[l] += r.count;
-      s->path_steps += res.path_steps;
-    }
-    // advance the drivers whose pass is complete
-    for (uint64_t id : in_batch) {
-      Query& qq = s->q[id];
-      if (pending_steps(qq) > 0.0) continue;
-      if (q_update(qq)) {
-        qq.t_done = now_s();
-        q_result(qq);
-        qq.state = 2;
-        s->free_slots.push_back(qq.slot);
-        qq.slot = -1;
-        s->done_order.push_back(id);
-        ++done;
-        ++s->completed;
-      }
-    }
-    std::vector<uint64_t> still;
-    for (uint64_t id : s->active)
-      if (s->q[id].state == 1) still.push_back(id);
-    s->active.swap(still);
   }
+  if (rc) return rc;
   s->ticks += 1;
   s->busy_s += now_s() - t0;
   if (n_done) *n_done = done;
@@ -463,10 +576,7 @@ int mlmc_server_stats(mlmc_server s, double out[6]) {
 
 int mlmc_server_destroy(mlmc_server s) {
   if (!s) return MLMC_OK;
-  if (s->h_models) cudaFreeHost(s->h_models);
-  if (s->h_reqs) cudaFreeHost(s->h_reqs);
-  if (s->h_results) cudaFreeHost(s->h_results);
-  delete s;
+  server_free(s);
   return MLMC_OK;
 }
 
