@@ -131,6 +131,14 @@ def fp32_peak_probe(torch, lib_probe=None):
     return best or None
 
 
+def workload_config(sched=None):
+    """The workload keys both arms report."""
+    sched = sched or workload()
+    return {"workload": "batched-multilevel-l0-12-bl600-baoab", "levels": "0..12",
+            "N_l": "1e9*10^(-l/2) (level 0: %d, level 12: %d)" % (sched[0][1], sched[-1][1]),
+            "path_steps_per_step": path_steps_of(sched), "integrator": "BAOAB"}
+
+
 def run_reference(args):
     """FP64 CPU oracle on a bounded sample of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -162,8 +170,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "batched-multilevel-l0-12-bl600-baoab (oracle sample)",
-                   "sample_scale": ORACLE_SAMPLE_SCALE, "path_steps_per_step": steps},
+        "config": dict(workload_config(), paths="fp64 (oracle)",
+                       sample="N_l x %g per step: %d path-steps" % (ORACLE_SAMPLE_SCALE, steps)),
         "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
@@ -374,14 +382,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "batched-multilevel-l0-12-bl600-baoab",
-                       "levels": "0..12", "N_l": "1e9*10^(-l/2) (level 0: %d, level 12: %d)"
-                       % (sched[0][1], sched[-1][1]),
-                       "path_steps_per_step": steps_per_step, "integrator": "BAOAB",
-                       "paths": "fp32", "sums": "fp64 Kahan",
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "tuning": tuning,
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": dict(workload_config(sched), paths="fp32", sums="fp64 Kahan",
+                           l2="flushed between timed steps (256 MB write)", tuning=tuning,
+                           parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (TRAFFIC["bytes_per_launch"]
