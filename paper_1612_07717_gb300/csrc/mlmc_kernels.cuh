@@ -300,17 +300,17 @@ __device__ __forceinline__ void multilevel_item_x2(const Model<float>& m, const 
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
                                                 uint64_t first, uint32_t count, Acc& acc) {
+  if constexpr (MLMC_X2 && std::is_same<R, float>::value) {
 #if MLMC_X2
-  if constexpr (std::is_same<R, float>::value) {
     multilevel_item_x2<INTEG, COUPLED>(m, lv, first, count, acc);
-    return;
-  }
 #endif
-  for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
-    Path<R> f, c;
-    bool bad;
-    run_pair<INTEG, R, COUPLED>(m, lv, first + j, f, c, bad, NoTrace<R>());
-    acc_add<R, COUPLED>(acc, m, f.z, c.z, bad);
+  } else {
+    for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
+      Path<R> f, c;
+      bool bad;
+      run_pair<INTEG, R, COUPLED>(m, lv, first + j, f, c, bad, NoTrace<R>());
+      acc_add<R, COUPLED>(acc, m, f.z, c.z, bad);
+    }
   }
 }
 
