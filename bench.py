@@ -209,26 +209,33 @@ def cpu_baseline_sample():
 
 def time_to_eps(G, W, torch, eps_frac=2.0 ** -10):
     """Wall time to RMSE eps = H * eps_frac on mean z(T): MLMC with FP32
-    BAOAB paths (the adaptive loop as one CUDA graph) against plain Monte
-    Carlo with FP64 symplectic-Euler paths at the timestep the SE hierarchy
-    needs for the same eps (its finest level)."""
+    BAOAB and GL paths (the adaptive loop as one CUDA graph; the faster one
+    is compared) against plain Monte Carlo with FP64 symplectic-Euler paths
+    at the timestep the SE hierarchy needs for the same eps (its finest
+    level)."""
     H = W.BL600["H"]
     eps = H * eps_frac
     out = {"eps_m": eps}
-    pb = G.make_params(W.bl600(G.BAOAB, L_max=14, n_init=10000), precision=G.FP32)
-    ws = G.Workspace(pb)
-    ge = G.GraphEstimator(eps, G.BAOAB, pb, 3, workspace=ws)
-    ge.launch(); ge.result()                        # warm-up (module load, first launch)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    ge.launch()
-    r = ge.result()
-    dt = time.perf_counter() - t
-    ge.close()
-    out["mlmc_fp32_baoab_graph"] = {"seconds": dt, "L": r["L"], "estimate_m": r["estimate"][0],
-                                    "rmse_stat_m": math.sqrt(r["est_variance"][0]),
-                                    "path_steps": r["total_path_steps"], "N": r["N"],
-                                    "converged": r["converged"]}
+    best = None
+    for name, integ in (("baoab", G.BAOAB), ("gl", G.GL)):
+        pb = G.make_params(W.bl600(integ, L_max=14, n_init=10000), precision=G.FP32)
+        ws = G.Workspace(pb)
+        ge = G.GraphEstimator(eps, integ, pb, 3, workspace=ws)
+        ge.launch(); ge.result()                    # warm-up (module load, first launch)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ge.launch()
+        r = ge.result()
+        dt_i = time.perf_counter() - t
+        ge.close()
+        out["mlmc_fp32_%s_graph" % name] = {
+            "seconds": dt_i, "L": r["L"], "estimate_m": r["estimate"][0],
+            "rmse_stat_m": math.sqrt(r["est_variance"][0]), "path_steps": r["total_path_steps"],
+            "N": r["N"], "converged": r["converged"]}
+        if best is None or dt_i < best[1]:
+            best = (name, dt_i)
+    out["mlmc_best"] = best[0]
+    dt = best[1]
     # the SE hierarchy's finest level for this eps sets the plain-MC timestep
     pse = G.make_params(W.bl600(G.SE, L_max=16, n_init=10000), precision=G.FP32)
     rse = G.estimate_graph(eps, G.SE, pse, 5, workspace=ws)
