@@ -17,13 +17,15 @@ Run on a GPU: ``python -m paper_1612_07717_gb300.sweeps [out.json]``.
 ``python -m paper_1612_07717_gb300.sweeps level se|gl|baoab LEVEL LOG2N X_ADAPT`` times
 one level-sums launch of the paper scenario (X_ADAPT 0: uniform timesteps),
 the unit a profiler capture of the level kernels is taken on.
+``python -m paper_1612_07717_gb300.sweeps time_to_eps`` times MLMC against
+plain FP64 Monte Carlo in the 600 m layer for eps = H 2^-9 .. H 2^-13.
 """
 import json
 import math
 import sys
 import time
 
-from . import (BAOAB, FP32, GL, SE, Workspace, estimate, estimate_graph, estimate_pdf,
+from . import (BAOAB, FP32, FP64, GL, SE, Workspace, estimate, estimate_graph, estimate_pdf,
                level_pdf_sums, make_params, stmc_estimate)
 from . import workloads as W
 
@@ -51,6 +53,43 @@ def stmc_cost(eps, integ, level, seed=2, n_pilot=4000, precision=FP32):
     dt = time.perf_counter() - t
     return dict(level=level, h=W.PAPER["T"] / (W.PAPER["M0"] << level), N=s["N"][0],
                 estimate=s["estimate"][0], path_steps=s["total_path_steps"], seconds=dt)
+
+
+def bl600_time_to_eps(eps_fracs=(2.0 ** -9, 2.0 ** -10, 2.0 ** -11, 2.0 ** -12, 2.0 ** -13),
+                      seed=3, n_init=2000, n_pilot=2000):
+    """Wall time to RMSE eps = H * frac on E[z(T)] in the 600 m layer: MLMC
+    with FP32 GL and BAOAB paths (the adaptive loop in one CUDA graph, after
+    one warm-up run) against plain Monte Carlo with FP64 symplectic-Euler
+    paths at the finest level the SE hierarchy needs for the same eps."""
+    import torch
+    H = W.BL600["H"]
+    out = []
+    # load the FP64 kernels before the first timed call
+    pw = make_params(W.bl600(SE), precision=FP64, level_min=8)
+    stmc_estimate(H * 2.0 ** -6, 8, SE, pw, seed + 400, n_pilot=n_pilot, workspace=Workspace(pw))
+    for frac in eps_fracs:
+        eps = H * frac
+        row = dict(eps_over_H=frac, eps_m=eps)
+        for name, integ in (("gl", GL), ("baoab", BAOAB)):
+            p = make_params(W.bl600(integ, L_max=14, n_init=n_init), precision=FP32)
+            ws = Workspace(p)
+            estimate_graph(eps, integ, p, seed + 100, workspace=ws)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = estimate_graph(eps, integ, p, seed, workspace=ws)
+            row["mlmc_" + name] = dict(seconds=time.perf_counter() - t, L=r["L"],
+                                       path_steps=r["total_path_steps"],
+                                       estimate_m=r["estimate"][0])
+        pse = make_params(W.bl600(SE, L_max=16, n_init=n_init), precision=FP32)
+        level = estimate_graph(eps, SE, pse, seed + 200, workspace=Workspace(pse))["L"]
+        p64 = make_params(W.bl600(SE), precision=FP64, level_min=level)
+        ws64 = Workspace(p64)
+        t = time.perf_counter()
+        s = stmc_estimate(eps, level, SE, p64, seed + 300, n_pilot=n_pilot, workspace=ws64)
+        row["stmc_fp64_se"] = dict(seconds=time.perf_counter() - t, level=level, N=s["N"][0],
+                                   path_steps=s["total_path_steps"], estimate_m=s["estimate"][0])
+        out.append(row)
+    return out
 
 
 def paper_cost_sweep(eps_list=EPS, integrators=(SE, GL, BAOAB)):
@@ -151,7 +190,9 @@ def time_level(integ, level, n, z_adapt=0.0, reps=3, seed=4):
                 path_steps_per_s=s["path_steps"] / (ms * 1e-3))
 
 
-if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "time_to_eps":
+    print(json.dumps(bl600_time_to_eps(), indent=1))
+elif __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
     integ = {"se": SE, "gl": GL, "baoab": BAOAB}[sys.argv[2]]
     print(json.dumps(time_level(integ, int(sys.argv[3]), 1 << int(sys.argv[4]),
                                 float(sys.argv[5]))))
