@@ -12,8 +12,9 @@
 namespace mlmc {
 
 // Launchers exported by the kernel translation units: prec_f32 / prec_f64
-// hold every kernel; prec_f32_b3 / prec_f32_b4 hold the persistent kernels
-// compiled for 3 and 4 resident blocks per SM (tighter register budgets).
+// hold every kernel; prec_f32_b3 / prec_f32_b4 / prec_f32_x2 / prec_f32_x2b3
+// hold the level-sums and persistent kernels of the other tuning variants
+// (tighter register budgets; two path pairs per thread).
 #define MLMC_DECLARE_MULTI(NS)                                                                 \
   namespace NS {                                                                               \
   cudaError_t multilevel(int, const HostModel&, const ReqPlan*, int, uint32_t, Partial*,      \
@@ -23,12 +24,13 @@ namespace mlmc {
   cudaError_t multilevel_table(int, const void*, size_t, const PlanReq*, int, uint32_t,       \
                                Partial*, unsigned int*, int, cudaStream_t);                     \
   int occupancy_multi(int);                                                                    \
+  int occupancy_sums(int);                                                                     \
+  cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t,         \
+                         Partial*, int, cudaStream_t);                                          \
   }
 #define MLMC_DECLARE_ALL(NS)                                                                   \
   MLMC_DECLARE_MULTI(NS)                                                                       \
   namespace NS {                                                                               \
-  cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t,         \
-                         Partial*, int, cudaStream_t);                                          \
   size_t model_size();                                                                         \
   void model_image(const HostModel&, void*);                                                   \
   cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*,       \
@@ -89,8 +91,7 @@ cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const Le
                               uint64_t N, uint64_t offset, Partial* partials, int grid,
                               cudaStream_t st) {
   if (hm.adapt) return launch_adapt_sums(prec, integ, hm, lv, N, offset, partials, grid, st);
-  return prec ? prec_f64::level_sums(integ, hm, lv, N, offset, partials, grid, st)
-              : prec_f32::level_sums(integ, hm, lv, N, offset, partials, grid, st);
+  MLMC_DISPATCH_MULTI(prec, integ, level_sums(integ, hm, lv, N, offset, partials, grid, st));
 }
 cudaError_t launch_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                               int n_req, uint32_t n_items, Partial* partials,
@@ -116,6 +117,9 @@ cudaError_t launch_multilevel_table(int prec, int integ, const void* models, siz
 static int occupancy_multi(int prec, int integ) {
   MLMC_DISPATCH_MULTI(prec, integ, occupancy_multi(integ));
 }
+static int occupancy_sums(int prec, int integ) {
+  MLMC_DISPATCH_MULTI(prec, integ, occupancy_sums(integ));
+}
 size_t model_bytes(int prec) { return prec ? prec_f64::model_size() : prec_f32::model_size(); }
 void model_image(int prec, const HostModel& hm, void* out) {
   if (prec) prec_f64::model_image(hm, out);
@@ -138,7 +142,7 @@ cudaError_t launch_pdf(int prec, int integ, const HostModel& hm, const LevelSpec
               : prec_f32::pdf(integ, hm, lv, N, offset, k, partials, grid, st);
 }
 int blocks_per_sm(int prec, int integ, bool multilevel) {
-  if (!multilevel) return prec ? prec_f64::occupancy(integ, false) : prec_f32::occupancy(integ, false);
+  if (!multilevel) return occupancy_sums(prec, integ);
   int nb = occupancy_multi(prec, integ);
   const int want = tune_of(prec, integ).blocks_per_sm;
   if (want > 0 && want < nb) nb = want;
@@ -461,9 +465,22 @@ int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
   int g = di.sms * blocks_per_sm(prec, integ, multilevel);
   if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
   if (!multilevel) {
-    const uint64_t need = (N + kBlock - 1) / kBlock;
+    const uint64_t per_block = min_item_paths(prec, integ);  // pairs of one pass of a block
+    const uint64_t need = (N + per_block - 1) / per_block;
     if (need < (uint64_t)g) g = (int)(need > 0 ? need : 1);
   }
+  return g;
+}
+
+// Grid of the adaptive level-sums kernel: blocks take contiguous pair ranges,
+// sized from the one-pair level kernel's occupancy.
+static int grid_adapt(int prec, int integ, uint64_t N) {
+  DevInfo di;
+  if (device_info(&di) != MLMC_OK) return 0;
+  int g = di.sms * (prec ? prec_f64::occupancy(integ, false) : prec_f32::occupancy(integ, false));
+  if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
+  const uint64_t need = (N + kBlock - 1) / kBlock;
+  if (need < (uint64_t)g) g = (int)(need > 0 ? need : 1);
   return g;
 }
 
@@ -633,7 +650,7 @@ int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
   if ((rc = carve(workspace, ws_bytes, &w))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = p->precision;
-  const int grid = grid_for(prec, integrator, false, N);
+  const int grid = hm.adapt ? grid_adapt(prec, integrator, N) : grid_for(prec, integrator, false, N);
   if (grid <= 0) return MLMC_ENODEV;
   if (N > (uint64_t)grid * kBlock * 0x7FFFFFFFull) return MLMC_EINVAL;  // per-thread counters
   rc = cuda_status(launch_level_sums(prec, integrator, hm, ls, N, path_offset, w.partials, grid, st));

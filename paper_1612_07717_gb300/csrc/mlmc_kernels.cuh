@@ -217,51 +217,6 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
   __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// Coupled-level sums
-// ---------------------------------------------------------------------------
-template <typename R>
-struct SumsArgs {
-  Model<R> m;
-  Level<R> lv;
-  uint64_t N, offset;
-  Partial* partials;
-};
-
-template <int INTEG, typename R, bool COUPLED>
-__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
-  Acc acc;
-  acc_zero(acc, a.m.qoi1_mode != 0);
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < a.N; j += stride) {
-    Path<R> f, c;
-    bool bad;
-    run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
-    acc_add<R, COUPLED>(acc, a.m, f.z, c.z, bad);
-  }
-  block_reduce_store(acc, COUPLED, a.m.qoi1_mode != 0, a.partials + blockIdx.x);
-}
-
-// ---------------------------------------------------------------------------
-// Persistent multi-level kernel
-// ---------------------------------------------------------------------------
-template <typename R>
-struct ReqDev {
-  Level<R> lv;
-  uint64_t first, count;
-  uint32_t item_paths, n_items, item_base, pad;
-};
-
-template <typename R>
-struct MultiArgs {
-  Model<R> m;
-  ReqDev<R> req[kMaxReq];
-  int32_t n_req;
-  uint32_t n_items;
-  Partial* partials;
-  unsigned int* counter;
-};
-
 #if MLMC_X2
 // Lane of a packed pair: the exact replay where the fast pass flagged a
 // multi-layer step, then the finiteness check, exactly as run_pair does.
@@ -296,6 +251,69 @@ __device__ __forceinline__ void multilevel_item_x2(const Model<float>& m, const 
   }
 }
 #endif
+
+// ---------------------------------------------------------------------------
+// Coupled-level sums
+// ---------------------------------------------------------------------------
+template <typename R>
+struct SumsArgs {
+  Model<R> m;
+  Level<R> lv;
+  uint64_t N, offset;
+  Partial* partials;
+};
+
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_level_sums(const __grid_constant__ SumsArgs<R> a) {
+  Acc acc;
+  acc_zero(acc, a.m.qoi1_mode != 0);
+  if constexpr (MLMC_X2 && std::is_same<R, float>::value) {
+#if MLMC_X2
+    // two pairs per thread: pairs 2g and 2g + 1 of global thread g, grid-stride
+    const StartX2 s0 = start_x2(a.m);
+    const uint64_t stride = 2 * (uint64_t)gridDim.x * kBlock;
+    for (uint64_t j = 2 * ((uint64_t)blockIdx.x * kBlock + threadIdx.x); j < a.N; j += stride) {
+      PathX2 f, c;
+      bool mx, my;
+      run_pair_x2_fast<INTEG, COUPLED>(a.m, a.lv, s0, a.offset + j, f, c, mx, my);
+      finish_lane<INTEG, COUPLED>(a.m, a.lv, a.offset + j, f.z.x, f.w.x, c.z.x, c.w.x, mx, acc);
+      if (j + 1 < a.N)
+        finish_lane<INTEG, COUPLED>(a.m, a.lv, a.offset + j + 1, f.z.y, f.w.y, c.z.y, c.w.y, my,
+                                    acc);
+    }
+#endif
+  } else {
+    const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+    for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < a.N; j += stride) {
+      Path<R> f, c;
+      bool bad;
+      run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
+      acc_add<R, COUPLED>(acc, a.m, f.z, c.z, bad);
+    }
+  }
+  block_reduce_store(acc, COUPLED, a.m.qoi1_mode != 0, a.partials + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent multi-level kernel
+// ---------------------------------------------------------------------------
+template <typename R>
+struct ReqDev {
+  Level<R> lv;
+  uint64_t first, count;
+  uint32_t item_paths, n_items, item_base, pad;
+};
+
+template <typename R>
+struct MultiArgs {
+  Model<R> m;
+  ReqDev<R> req[kMaxReq];
+  int32_t n_req;
+  uint32_t n_items;
+  Partial* partials;
+  unsigned int* counter;
+};
+
 
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
