@@ -36,8 +36,8 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # taken with (their SHA-1, see kernel_sha1): DRAM bytes per full-size launch
 # (launch list) and, from the full capture of the 1e8-path case, the FMA-pipe
 # and issue-slot activity and the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "e0a77305a3edaed96060fcbadf2df4b1644f22bc", "bytes_per_launch": 0.902e6,
-           "fma_pipe_active_pct": 54.4, "issue_active_pct": 68.1,
+TRAFFIC = {"kernel_sha1": "ee546d412bc59a9f60e73fb356f16a842919474f", "bytes_per_launch": 0.923e6,
+           "fma_pipe_active_pct": 54.5, "issue_active_pct": 68.0,
            "thread_inst_per_path_step": 68.9}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
