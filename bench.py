@@ -34,11 +34,12 @@ N0 = 1e9
 FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # ncu figures of the path kernel, valid only for the kernel sources they were
 # taken with (their SHA-1, see kernel_sha1): DRAM bytes per full-size launch
-# (launch list) and, from the full capture of the 1e8-path case, the FMA-pipe
-# and issue-slot activity and the thread instructions per path-step.
+# (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
+# full-size launch (one-pass metric captures) and, from the full capture of the
+# 1e8-path case, the thread instructions per path-step.
 TRAFFIC = {"kernel_sha1": "ee546d412bc59a9f60e73fb356f16a842919474f", "bytes_per_launch": 0.923e6,
-           "fma_pipe_active_pct": 54.5, "issue_active_pct": 68.0,
-           "thread_inst_per_path_step": 68.9}
+           "fma_pipe_active_pct": 56.9, "fmaheavy_pipe_active_pct": 62.4,
+           "issue_active_pct": 70.2, "thread_inst_per_path_step": 68.9}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
@@ -399,7 +400,9 @@ def main():
                          "peak_source": "measured FFMA probe" if peak_probe else
                          "derived SMs*128*2*clock at %.0f MHz" % sm_mhz,
                          "flops_per_path_step": FLOPS_PER_PATH_STEP,
-                         "ncu": ({k: TRAFFIC[k] for k in ("fma_pipe_active_pct", "issue_active_pct",
+                         "ncu": ({k: TRAFFIC[k] for k in ("fma_pipe_active_pct",
+                                                          "fmaheavy_pipe_active_pct",
+                                                          "issue_active_pct",
                                                           "thread_inst_per_path_step")}
                                  if TRAFFIC["kernel_sha1"] == kernel_sha1() else None),
                          # one instruction per SM sub-partition per cycle at the
