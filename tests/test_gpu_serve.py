@@ -113,3 +113,18 @@ def test_sampled_queries_match_the_fp64_oracle():
           % (len(ratios), rmse_over_eps))
     assert len(ratios) >= 10
     assert rmse_over_eps <= 1.25, ratios
+
+
+def test_idle_ticks_and_closing_with_launches_in_flight():
+    srv = G.Server(max_active=4)
+    assert srv.tick() == (0, 0)                          # nothing queued: returns at once
+    qs = S.draw_queries(12, seed=9)
+    ids = [srv.submit(G.make_params(d), eps) for _, d, eps in qs]
+    srv.tick()
+    srv.tick()                                           # launches now in flight
+    srv.close()                                          # waits for them, frees everything
+    again = G.Server(max_active=4)                       # the device is still usable
+    again.submit(G.make_params(qs[0][1]), qs[0][2])
+    again.run_until_idle()
+    assert again.stats()["finished"] == 1
+    assert len(ids) == 12
