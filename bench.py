@@ -37,7 +37,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "ee546d412bc59a9f60e73fb356f16a842919474f", "bytes_per_launch": 0.923e6,
+TRAFFIC = {"kernel_sha1": "74261a424aa94d15f25e1b2ff8d030d0c52669fe", "bytes_per_launch": 1.078e6,
            "fma_pipe_active_pct": 56.9, "fmaheavy_pipe_active_pct": 62.4,
            "issue_active_pct": 70.2, "thread_inst_per_path_step": 68.9}
 # The sources the persistent FP32 path kernels are compiled from.

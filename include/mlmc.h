@@ -167,8 +167,8 @@ const char* mlmc_strerror(int code);
  * device is visible. */
 int mlmc_device_info(int32_t out[3]);
 
-/* Tuning of the persistent multi-level kernels for one (integrator,
- * precision): `variant` selects the compiled kernel: 1 (uncapped), 3 or 4
+/* Tuning of the level-sums and persistent multi-level kernels for one
+ * (integrator, precision): `variant` selects the compiled kernel: 1 (uncapped), 3 or 4
  * = one path pair per thread, compiled for that many resident blocks per
  * SM; 12 or 13 = two path pairs per thread on the packed FP32
  * instructions, compiled for 2 or 3 blocks per SM (FP32 only; per-path
@@ -199,8 +199,9 @@ size_t mlmc_workspace_bytes(const mlmc_params* p, int max_requests);
 /* ------------------------------------------------------------ estimation */
 /* Sums of N coupled pairs of `level` (plain paths on level_min), paths
  * [path_offset, path_offset + N); Section 3.3, Eq. (Yhatell).  Launches the
- * coupled-level kernel and the fixed-order reduction on `stream`, copies the
- * sums into *out and synchronises the stream.  Returns MLMC_ENONFINITE (with
+ * coupled-level kernel (the variant the tuning table names) and the
+ * fixed-order reduction on `stream`, copies the sums into *out and
+ * synchronises the stream.  Returns MLMC_ENONFINITE (with
  * valid *out) if any pair diverged, MLMC_EUNSTABLE for an unstable SE level
  * unless p->allow_unstable. */
 int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
