@@ -18,7 +18,9 @@ Run on a GPU: ``python -m paper_1612_07717_gb300.sweeps [out.json]``.
 one level-sums launch of the paper scenario (X_ADAPT 0: uniform timesteps),
 the unit a profiler capture of the level kernels is taken on.
 ``python -m paper_1612_07717_gb300.sweeps time_to_eps`` times MLMC against
-plain FP64 Monte Carlo in the 600 m layer for eps = H 2^-9 .. H 2^-13.
+plain FP64 Monte Carlo in the 600 m layer for eps = H 2^-9 .. H 2^-13;
+``python -m paper_1612_07717_gb300.sweeps scenarios`` runs the integrator and
+precision sweep over (u*, z0 / H, T).
 """
 import json
 import math
@@ -89,6 +91,41 @@ def bl600_time_to_eps(eps_fracs=(2.0 ** -9, 2.0 ** -10, 2.0 ** -11, 2.0 ** -12, 
         row["stmc_fp64_se"] = dict(seconds=time.perf_counter() - t, level=level, N=s["N"][0],
                                    path_steps=s["total_path_steps"], estimate_m=s["estimate"][0])
         out.append(row)
+    return out
+
+
+def scenario_precision_sweep(u_stars=(0.1, 0.2, 0.4), z0_fracs=(0.01, 0.1, 0.5),
+                             Ts=(300.0, 600.0, 1800.0), eps_frac=2.0 ** -8, seed=17):
+    """The integrator and precision sweep of the 1-D boundary layer: for
+    every (u*, z0 / H, T) with H = 0.3 u* / f and each integrator, the MLMC
+    estimate of E[z(T)] to eps = H eps_frac with FP32 paths and with FP64
+    paths (FP64 sums in both; the whole loop in one CUDA graph); SE starts at
+    its stable level.  Returns one record per (scenario, integrator) with
+    both estimates, their standard errors and |difference| / combined SE."""
+    from . import stable_level_min
+    out = []
+    for u in u_stars:
+        for zf in z0_fracs:
+            for T in Ts:
+                H = 0.3 * u / W.BL600["f_coriolis"]
+                for integ in (SE, GL, BAOAB):
+                    d = W.bl600(integ, u_star=u, H=H, z0=zf * H, T=T, qoi_threshold=0.1 * H,
+                                L_max=12, n_init=4000)
+                    d["level_min"] = stable_level_min(make_params(d), integ)
+                    row = dict(u_star=u, z0_over_H=zf, T=T, H=H, integrator=NAMES[integ],
+                               level_min=d["level_min"])
+                    for name, prec in (("fp32", FP32), ("fp64", FP64)):
+                        p = make_params(d, precision=prec)
+                        t = time.perf_counter()
+                        r = estimate_graph(H * eps_frac, integ, p, seed, workspace=Workspace(p))
+                        row[name] = dict(estimate=r["estimate"][0],
+                                         se=math.sqrt(r["est_variance"][0]), L=r["L"],
+                                         converged=r["converged"],
+                                         path_steps=r["total_path_steps"],
+                                         seconds=time.perf_counter() - t)
+                    row["z"] = abs(row["fp32"]["estimate"] - row["fp64"]["estimate"]) / math.sqrt(
+                        row["fp32"]["se"] ** 2 + row["fp64"]["se"] ** 2)
+                    out.append(row)
     return out
 
 
@@ -190,7 +227,9 @@ def time_level(integ, level, n, z_adapt=0.0, reps=3, seed=4):
                 path_steps_per_s=s["path_steps"] / (ms * 1e-3))
 
 
-if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "time_to_eps":
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "scenarios":
+    print(json.dumps(scenario_precision_sweep(), indent=1))
+elif __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "time_to_eps":
     print(json.dumps(bl600_time_to_eps(), indent=1))
 elif __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
     integ = {"se": SE, "gl": GL, "baoab": BAOAB}[sys.argv[2]]
