@@ -37,7 +37,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "74261a424aa94d15f25e1b2ff8d030d0c52669fe", "bytes_per_launch": 1.078e6,
+TRAFFIC = {"kernel_sha1": "7a0bb3013fb4d7921bed127d04052bc29f755ab4", "bytes_per_launch": 1.078e6,
            "fma_pipe_active_pct": 56.9, "fmaheavy_pipe_active_pct": 62.4,
            "issue_active_pct": 70.2, "thread_inst_per_path_step": 68.9}
 # The sources the persistent FP32 path kernels are compiled from.
@@ -54,12 +54,23 @@ KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h
 
 
 def kernel_sha1():
+    """SHA-1 of KERNEL_SOURCES with comments and whitespace removed: it
+    changes with the code the kernels are compiled from, not with their
+    documentation."""
     import hashlib
+    import re
+    token = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\s+', re.S)
+
+    def code(text):
+        return token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else
+                         ("" if m.group(0)[0] in "/" else " "), text)
     h = hashlib.sha1()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        with open(os.path.join(ROOT, name), encoding="utf-8") as f:
+            h.update(name.encode() + b"\0" + code(f.read()).encode())
     return h.hexdigest()
+
+
 ORACLE_SAMPLE_SCALE = 2e-3
 
 

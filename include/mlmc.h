@@ -363,7 +363,9 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  *                        chunk enters its query in chunk order; a query
  *                        whose pass is folded advances its driver and may
  *                        finish.  n_done: queries finished in this call;
- *                        n_active: queries left (active and queued)
+ *                        n_active: queries left (active and queued).  After
+ *                        a CUDA error every later call returns that error
+ *                        (launches in flight may be lost)
  *   mlmc_server_poll     1 while the query runs; its final status (MLMC_OK,
  *                        MLMC_ENOTCONV, MLMC_ENONFINITE) with the result and
  *                        its submit-to-finish latency once done

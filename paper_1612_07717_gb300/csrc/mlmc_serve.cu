@@ -221,6 +221,7 @@ struct mlmc_server_s {
   std::vector<uint64_t> active;              // admission order
   std::vector<uint64_t> to_upload;           // admitted, Model not yet on the device
   std::vector<int> free_slots;
+  int failed = MLMC_OK;                      // first CUDA error: the server stops
   // statistics
   uint64_t ticks = 0, path_steps = 0, completed = 0;
   double busy_s = 0.0;
@@ -517,6 +518,7 @@ int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t
 // least once while any query is active.
 int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
   if (!s) return MLMC_EINVAL;
+  if (s->failed) return s->failed;  // launches in flight may be lost: do not fold them
   const double t0 = now_s();
   int done = 0, rc = MLMC_OK;
   bool folded = true, launched = false;
@@ -536,7 +538,10 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
       rc = issue(s, &launched);
     }
   }
-  if (rc) return rc;
+  if (rc) {
+    s->failed = rc;
+    return rc;
+  }
   s->ticks += 1;
   s->busy_s += now_s() - t0;
   if (n_done) *n_done = done;
