@@ -280,6 +280,48 @@ int mlmc_estimate_sharded(double eps, int integrator, const mlmc_params* p, uint
                           int rank, int world, mlmc_allreduce_fn reduce, void* ctx,
                           void* workspace, size_t ws_bytes, void* stream, mlmc_result* out);
 
+/* The host-driven estimate one pass at a time, for checkpoint and resume.
+ * The driver's whole state is the plain struct below (no pointers): it can
+ * be copied, written to a file and read back in another process, and a run
+ * resumed from it continues exactly as the uninterrupted one, because every
+ * pass's launch depends only on the state (path indices continue from
+ * n_done, the RNG is keyed by path index).
+ *   mlmc_estimate_begin   validates the arguments and starts a state at
+ *                         level_min (no device work)
+ *   mlmc_estimate_pass    runs the next pass -- the new level's n_init
+ *                         samples, or the top-up of every level to Eq. 12's
+ *                         N_l followed by the bias test -- as one
+ *                         mlmc_multilevel_sums launch on `stream`, and
+ *                         synchronises it; returns 1 once the estimate is
+ *                         complete (then does nothing), MLMC_OK while passes
+ *                         remain, or an error (the state is then unchanged)
+ *   mlmc_estimate_result  the result of the state (any time; final once
+ *                         complete), with mlmc_estimate's return codes
+ * mlmc_estimate runs exactly these steps, so the three give its result bit
+ * for bit. */
+typedef struct mlmc_estimate_state {
+  double eps;                                   /* RMSE target                   */
+  uint64_t seed;
+  int32_t integrator;
+  int32_t L;                                    /* finest level so far           */
+  int32_t phase;                                /* 0 new level next, 1 top-up
+                                                   next, 2 complete              */
+  int32_t converged;                            /* 1 if the bias test passed     */
+  uint64_t n_done[MLMC_MAX_LEVELS];             /* samples issued per level      */
+  uint64_t n[MLMC_MAX_LEVELS];                  /* finite pairs in the sums      */
+  uint64_t n_nonfinite[MLMC_MAX_LEVELS];
+  uint64_t path_steps[MLMC_MAX_LEVELS];
+  double sum[MLMC_MAX_LEVELS][2][6];            /* as mlmc_level_result.sum      */
+  double seconds;                               /* wall time of the passes run   */
+  int32_t passes;                               /* passes run                    */
+  int32_t reserved;
+} mlmc_estimate_state;
+int mlmc_estimate_begin(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                        mlmc_estimate_state* st);
+int mlmc_estimate_pass(mlmc_estimate_state* st, const mlmc_params* p, void* workspace,
+                       size_t ws_bytes, void* stream);
+int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, mlmc_result* out);
+
 /* The same adaptive estimate with the whole loop on the device, as one CUDA
  * graph: an init kernel, then a conditional while-node whose body is the
  * persistent multi-level kernel over the levels that need samples, the

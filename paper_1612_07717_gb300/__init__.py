@@ -59,6 +59,17 @@ class Result(C.Structure):
                 ("n_nonfinite", C.c_uint64), ("seconds", C.c_double)]
 
 
+class EstimateState(C.Structure):
+    """``mlmc_estimate_state``: the host-driven estimator's whole state."""
+    _fields_ = [("eps", C.c_double), ("seed", C.c_uint64), ("integrator", C.c_int32),
+                ("L", C.c_int32), ("phase", C.c_int32), ("converged", C.c_int32),
+                ("n_done", C.c_uint64 * MAX_LEVELS), ("n", C.c_uint64 * MAX_LEVELS),
+                ("n_nonfinite", C.c_uint64 * MAX_LEVELS),
+                ("path_steps", C.c_uint64 * MAX_LEVELS),
+                ("sum", ((C.c_double * 6) * 2) * MAX_LEVELS), ("seconds", C.c_double),
+                ("passes", C.c_int32), ("reserved", C.c_int32)]
+
+
 class LevelRequest(C.Structure):
     _fields_ = [("level", C.c_int32), ("reserved", C.c_int32), ("first", C.c_uint64),
                 ("count", C.c_uint64)]
@@ -99,6 +110,12 @@ def lib():
                                            u64, vp, C.c_size_t, vp, C.POINTER(LevelResult)]
         L.mlmc_estimate.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t, vp,
                                     C.POINTER(Result)]
+        L.mlmc_estimate_begin.argtypes = [C.c_double, i32, C.POINTER(Params), u64,
+                                          C.POINTER(EstimateState)]
+        L.mlmc_estimate_pass.argtypes = [C.POINTER(EstimateState), C.POINTER(Params), vp,
+                                         C.c_size_t, vp]
+        L.mlmc_estimate_result.argtypes = [C.POINTER(EstimateState), C.POINTER(Params),
+                                           C.POINTER(Result)]
         L.mlmc_estimate_sharded.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, i32,
                                             ALLREDUCE_FN, vp, vp, C.c_size_t, vp,
                                             C.POINTER(Result)]
@@ -285,6 +302,90 @@ def estimate(eps, integrator, params, seed, workspace=None, stream=None):
     out = _result(r, params.level_min)
     out["status"] = rc
     return out
+
+
+class Estimation:
+    """The host-driven estimate one pass at a time (``mlmc_estimate_begin``,
+    ``mlmc_estimate_pass``, ``mlmc_estimate_result``), with a JSON checkpoint
+    of its state: ``state_dict`` / ``from_state_dict``, or ``run(checkpoint=
+    path)`` which writes the state after every pass and resumes from the
+    file when it exists.  A resumed run gives the uninterrupted result bit
+    for bit (floats are written with their exact repr)."""
+
+    def __init__(self, eps, integrator, params, seed, workspace=None, stream=None):
+        self.params = params
+        self.workspace = workspace or Workspace(params)
+        self.stream = stream
+        self.state = EstimateState()
+        _check(lib().mlmc_estimate_begin(eps, integrator, C.byref(params), seed,
+                                         C.byref(self.state)), "mlmc_estimate_begin")
+
+    @property
+    def done(self):
+        return self.state.phase == 2
+
+    def step(self):
+        """Run the next pass; True once the estimate is complete."""
+        rc = lib().mlmc_estimate_pass(C.byref(self.state), C.byref(self.params),
+                                      *self.workspace.args(), _stream_handle(self.stream))
+        if rc == 1:
+            return True
+        _check(rc, "mlmc_estimate_pass")
+        return False
+
+    def result(self):
+        r = Result()
+        rc = lib().mlmc_estimate_result(C.byref(self.state), C.byref(self.params), C.byref(r))
+        _check(rc, "mlmc_estimate_result", allow=(ENONFINITE, ENOTCONV))
+        out = _result(r, self.params.level_min)
+        out["status"] = rc
+        return out
+
+    def state_dict(self):
+        st = self.state
+        d = {}
+        for name, _ in EstimateState._fields_:
+            v = getattr(st, name)
+            if name == "sum":
+                d[name] = [[list(v[l][q]) for q in range(2)] for l in range(MAX_LEVELS)]
+            elif isinstance(v, (int, float)):
+                d[name] = v
+            else:
+                d[name] = list(v)
+        return d
+
+    def load_state_dict(self, d):
+        st = EstimateState()
+        for name, _ in EstimateState._fields_:
+            v = d[name]
+            if name == "sum":
+                for l in range(MAX_LEVELS):
+                    for q in range(2):
+                        for k in range(6):
+                            st.sum[l][q][k] = float(v[l][q][k])
+            elif isinstance(v, list):
+                arr = getattr(st, name)
+                for k, x in enumerate(v):
+                    arr[k] = x
+            else:
+                setattr(st, name, v)
+        self.state = st
+
+    def run(self, checkpoint=None):
+        """Run to completion; with a checkpoint path, resume from it if it
+        exists and rewrite it after every pass."""
+        import json
+        if checkpoint and os.path.exists(checkpoint):
+            with open(checkpoint) as f:
+                self.load_state_dict(json.load(f))
+        while not self.done:
+            self.step()
+            if checkpoint:
+                tmp = checkpoint + ".tmp"
+                with open(tmp, "w") as f:
+                    json.dump(self.state_dict(), f)
+                os.replace(tmp, checkpoint)
+        return self.result()
 
 
 def torch_allreduce(group=None):

@@ -802,110 +802,126 @@ struct Shard {
 };
 constexpr int kShardWidth = 16;  // doubles per level in the reduced buffer
 
-static int estimate_impl(double eps, int integrator, const mlmc_params* p, uint64_t seed,
-                         void* workspace, size_t ws_bytes, void* stream, mlmc_result* out,
-                         const Shard& sh) {
-  if (!out || !p || !(eps > 0.0)) return MLMC_EINVAL;
-  if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2)
-    return MLMC_EINVAL;
-  if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world || (sh.world > 1 && !sh.reduce))
-    return MLMC_EINVAL;
+// The host-driven estimate is a state machine over mlmc_estimate_state:
+// phase 0 runs the new level's n_init samples, phase 1 the top-up of every
+// level to Eq. 12's N_l and then the bias test (Eq. 11), which either ends
+// the estimate or adds a level.  Each pass is one multi-level launch over
+// this rank's contiguous slice of every level's new path range, followed by
+// the all-reduce of the sharded form; the state changes only when the pass
+// succeeded on every rank.
+static int estimate_pass_impl(mlmc_estimate_state* st, const mlmc_params* p, void* workspace,
+                              size_t ws_bytes, void* stream, const Shard& sh) {
+  if (!st || !p) return MLMC_EINVAL;
+  if (st->phase == 2) return 1;
+  if (st->phase != 0 && st->phase != 1) return MLMC_EINVAL;
+  const int lmin = p->level_min, L = st->L;
+  if (L < lmin || L > p->L_max || L >= MLMC_MAX_LEVELS) return MLMC_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
-  double buf[MLMC_MAX_LEVELS * kShardWidth];
-  mlmc_level_result S[MLMC_MAX_LEVELS];
-  uint64_t Ndone[MLMC_MAX_LEVELS] = {0}, dN[MLMC_MAX_LEVELS] = {0};
-  double V[MLMC_MAX_LEVELS] = {0}, C[MLMC_MAX_LEVELS] = {0};
-  std::memset(S, 0, sizeof(S));
-  const int lmin = p->level_min;
-  int L = lmin, converged = 0, status = MLMC_OK;
-  for (;;) {
+  const double eps = st->eps;
+  uint64_t dN[MLMC_MAX_LEVELS] = {0};
+  if (st->phase == 0) {
     dN[L] = (uint64_t)p->n_init;
-    for (int pass = 0; pass < 2; ++pass) {
-      // this rank's contiguous slice of every level's [Ndone, Ndone + dN),
-      // all levels of the pass in one multi-level launch
-      int err = MLMC_OK;
-      mlmc_level_request rq[MLMC_MAX_LEVELS];
-      int nrq = 0;
-      for (int l = lmin; l <= L; ++l) {
-        double* b = buf + (l - lmin) * kShardWidth;
-        for (int k = 0; k < kShardWidth; ++k) b[k] = 0.0;
-        if (!dN[l]) continue;
-        const uint64_t share = dN[l] / (uint64_t)sh.world, rem = dN[l] % (uint64_t)sh.world;
-        const uint64_t r_ = (uint64_t)sh.rank;
-        const uint64_t cnt = share + (r_ < rem ? 1 : 0);
-        const uint64_t first = Ndone[l] + r_ * share + (r_ < rem ? r_ : rem);
-        if (!cnt) continue;
-        rq[nrq].level = l;
-        rq[nrq].reserved = 0;
-        rq[nrq].first = first;
-        rq[nrq].count = cnt;
-        ++nrq;
-      }
-      if (nrq) {
-        mlmc_level_result res[MLMC_MAX_LEVELS];
-        int rc = mlmc_multilevel_sums(rq, nrq, integrator, p, seed, workspace, ws_bytes, stream,
-                                      res);
-        if (rc && rc != MLMC_ENONFINITE) err = rc;
-        for (int k = 0; k < nrq && !err; ++k) {
-          double* b = buf + (rq[k].level - lmin) * kShardWidth;
-          b[0] = (double)res[k].n;
-          b[1] = (double)res[k].n_nonfinite;
-          b[2] = (double)res[k].path_steps;
-          for (int q = 0; q < 2; ++q)
-            for (int j = 0; j < 6; ++j) b[3 + 6 * q + j] = res[k].sum[q][j];
-        }
-      }
-      const int nl = L - lmin + 1;
-      buf[nl * kShardWidth - 1] = err ? 1.0 : 0.0;   // last slot of the last level: error flag
-      if (sh.world > 1) {
-        if (sh.reduce(buf, nl * kShardWidth, sh.ctx) != 0) return MLMC_ECOMM;
-      }
-      if (buf[nl * kShardWidth - 1] != 0.0) return err ? err : MLMC_ECOMM;  // a rank failed
-      for (int l = lmin; l <= L; ++l) {
-        const double* b = buf + (l - lmin) * kShardWidth;
-        if (!dN[l]) continue;
-        S[l].n += (uint64_t)b[0];
-        S[l].n_nonfinite += (uint64_t)b[1];
-        S[l].path_steps += (uint64_t)b[2];
-        for (int q = 0; q < 2; ++q)
-          for (int k = 0; k < 6; ++k) S[l].sum[q][k] += b[3 + 6 * q + k];
-        if (b[1] > 0.0) status = MLMC_ENONFINITE;
-        Ndone[l] += dN[l];
-        dN[l] = 0;
-      }
-      if (pass == 1) break;
-      double total = 0.0;
-      for (int l = lmin; l <= L; ++l) {
-        const double n = (double)S[l].n;
-        const double m1 = S[l].sum[0][0], m2 = S[l].sum[0][1];
-        V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
-        if (V[l] < 0.0) V[l] = 0.0;
-        // C_l: integrator steps of one sample, M + M/2 with uniform timesteps
-        // (M on level_min) and the counted mean with adaptive ones
-        C[l] = (double)S[l].path_steps / (double)(S[l].n + S[l].n_nonfinite);
-        total += std::sqrt(V[l] * C[l]);
-      }
-      for (int l = lmin; l <= L; ++l) {
-        const double Nopt = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * total);
-        dN[l] = Nopt > (double)Ndone[l] ? (uint64_t)(Nopt - (double)Ndone[l]) : 0;
-      }
+  } else {
+    double V[MLMC_MAX_LEVELS] = {0}, Cl[MLMC_MAX_LEVELS] = {0}, total = 0.0;
+    for (int l = lmin; l <= L; ++l) {
+      const double n = (double)st->n[l];
+      const double m1 = st->sum[l][0][0], m2 = st->sum[l][0][1];
+      V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
+      if (V[l] < 0.0) V[l] = 0.0;
+      // C_l: integrator steps of one sample, M + M/2 with uniform timesteps
+      // (M on level_min) and the counted mean with adaptive ones
+      Cl[l] = (double)st->path_steps[l] / (double)(st->n[l] + st->n_nonfinite[l]);
+      total += std::sqrt(V[l] * Cl[l]);
     }
-    if (L >= lmin + 2) {
-      const double yL = std::fabs(S[L].sum[0][0] / (double)S[L].n);
-      const double yL1 = std::fabs(S[L - 1].sum[0][0] / (double)S[L - 1].n);
-      if (std::fmax(yL1 / 2.0, yL) < eps / std::sqrt(2.0)) { converged = 1; break; }
+    for (int l = lmin; l <= L; ++l) {
+      const double Nopt = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / Cl[l]) * total);
+      dN[l] = Nopt > (double)st->n_done[l] ? (uint64_t)(Nopt - (double)st->n_done[l]) : 0;
     }
-    if (L >= p->L_max) break;
-    L += 1;
   }
+  double buf[MLMC_MAX_LEVELS * kShardWidth];
+  int err = MLMC_OK;
+  mlmc_level_request rq[MLMC_MAX_LEVELS];
+  int nrq = 0;
+  for (int l = lmin; l <= L; ++l) {
+    double* b = buf + (l - lmin) * kShardWidth;
+    for (int k = 0; k < kShardWidth; ++k) b[k] = 0.0;
+    if (!dN[l]) continue;
+    const uint64_t share = dN[l] / (uint64_t)sh.world, rem = dN[l] % (uint64_t)sh.world;
+    const uint64_t r_ = (uint64_t)sh.rank;
+    const uint64_t cnt = share + (r_ < rem ? 1 : 0);
+    const uint64_t first = st->n_done[l] + r_ * share + (r_ < rem ? r_ : rem);
+    if (!cnt) continue;
+    rq[nrq].level = l;
+    rq[nrq].reserved = 0;
+    rq[nrq].first = first;
+    rq[nrq].count = cnt;
+    ++nrq;
+  }
+  if (nrq) {
+    mlmc_level_result res[MLMC_MAX_LEVELS];
+    int rc = mlmc_multilevel_sums(rq, nrq, st->integrator, p, st->seed, workspace, ws_bytes,
+                                  stream, res);
+    if (rc && rc != MLMC_ENONFINITE) err = rc;
+    for (int k = 0; k < nrq && !err; ++k) {
+      double* b = buf + (rq[k].level - lmin) * kShardWidth;
+      b[0] = (double)res[k].n;
+      b[1] = (double)res[k].n_nonfinite;
+      b[2] = (double)res[k].path_steps;
+      for (int q = 0; q < 2; ++q)
+        for (int j = 0; j < 6; ++j) b[3 + 6 * q + j] = res[k].sum[q][j];
+    }
+  }
+  const int nl = L - lmin + 1;
+  buf[nl * kShardWidth - 1] = err ? 1.0 : 0.0;   // last slot of the last level: error flag
+  if (sh.world > 1) {
+    if (sh.reduce(buf, nl * kShardWidth, sh.ctx) != 0) return MLMC_ECOMM;
+  }
+  if (buf[nl * kShardWidth - 1] != 0.0) return err ? err : MLMC_ECOMM;  // a rank failed
+  for (int l = lmin; l <= L; ++l) {
+    const double* b = buf + (l - lmin) * kShardWidth;
+    if (!dN[l]) continue;
+    st->n[l] += (uint64_t)b[0];
+    st->n_nonfinite[l] += (uint64_t)b[1];
+    st->path_steps[l] += (uint64_t)b[2];
+    for (int q = 0; q < 2; ++q)
+      for (int k = 0; k < 6; ++k) st->sum[l][q][k] += b[3 + 6 * q + k];
+    st->n_done[l] += dN[l];
+  }
+  if (st->phase == 0) {
+    st->phase = 1;
+  } else {
+    bool conv = false;
+    if (L >= lmin + 2) {
+      const double yL = std::fabs(st->sum[L][0][0] / (double)st->n[L]);
+      const double yL1 = std::fabs(st->sum[L - 1][0][0] / (double)st->n[L - 1]);
+      conv = std::fmax(yL1 / 2.0, yL) < eps / std::sqrt(2.0);
+    }
+    if (conv || L >= p->L_max) {
+      st->converged = conv ? 1 : 0;
+      st->phase = 2;
+    } else {
+      st->L = L + 1;
+      st->phase = 0;
+    }
+  }
+  st->passes += 1;
+  st->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st->phase == 2 ? 1 : MLMC_OK;
+}
+
+static int estimate_result_impl(const mlmc_estimate_state* st, const mlmc_params* p,
+                                mlmc_result* out) {
+  if (!st || !p || !out) return MLMC_EINVAL;
+  const int lmin = p->level_min, L = st->L;
+  if (L < lmin || L >= MLMC_MAX_LEVELS) return MLMC_EINVAL;
   std::memset(out, 0, sizeof(*out));
   out->L = L;
-  out->converged = converged;
+  out->converged = st->converged;
   for (int q = 0; q < 2; ++q) {
     double est = 0.0, var = 0.0;
     for (int l = lmin; l <= L; ++l) {
-      const double n = (double)S[l].n;
-      const double m1 = S[l].sum[q][0], m2 = S[l].sum[q][1];
+      const double n = (double)st->n[l];
+      const double m1 = st->sum[l][q][0], m2 = st->sum[l][q][1];
       est += m1 / n;
       const double v = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
       var += (v > 0.0 ? v : 0.0) / n;
@@ -913,18 +929,59 @@ static int estimate_impl(double eps, int integrator, const mlmc_params* p, uint6
     out->estimate[q] = est;
     out->est_variance[q] = var;
   }
+  bool nonfinite = false;
   for (int l = lmin; l <= L; ++l) {
-    const double n = (double)S[l].n;
-    out->N[l] = S[l].n;
-    out->mean_y[l] = S[l].sum[0][0] / n;
-    const double v = n > 1.0 ? (S[l].sum[0][1] - S[l].sum[0][0] * S[l].sum[0][0] / n) / (n - 1.0) : 0.0;
+    const double n = (double)st->n[l];
+    out->N[l] = st->n[l];
+    out->mean_y[l] = st->sum[l][0][0] / n;
+    const double v =
+        n > 1.0 ? (st->sum[l][0][1] - st->sum[l][0][0] * st->sum[l][0][0] / n) / (n - 1.0) : 0.0;
     out->V[l] = v > 0.0 ? v : 0.0;
-    out->total_path_steps += S[l].path_steps;
-    out->n_nonfinite += S[l].n_nonfinite;
+    out->total_path_steps += st->path_steps[l];
+    out->n_nonfinite += st->n_nonfinite[l];
+    nonfinite |= st->n_nonfinite[l] > 0;
   }
-  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (status) return status;
-  return converged ? MLMC_OK : MLMC_ENOTCONV;
+  out->seconds = st->seconds;
+  if (nonfinite) return MLMC_ENONFINITE;
+  return st->converged ? MLMC_OK : MLMC_ENOTCONV;
+}
+
+static int estimate_impl(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                         void* workspace, size_t ws_bytes, void* stream, mlmc_result* out,
+                         const Shard& sh) {
+  if (!out) return MLMC_EINVAL;
+  if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world || (sh.world > 1 && !sh.reduce))
+    return MLMC_EINVAL;
+  mlmc_estimate_state st;
+  int rc = mlmc_estimate_begin(eps, integrator, p, seed, &st);
+  while (rc == MLMC_OK) rc = estimate_pass_impl(&st, p, workspace, ws_bytes, stream, sh);
+  if (rc != 1) return rc;
+  return estimate_result_impl(&st, p, out);
+}
+
+int mlmc_estimate_begin(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                        mlmc_estimate_state* st) {
+  if (!st || !p || !(eps > 0.0)) return MLMC_EINVAL;
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2 ||
+      p->level_min < 0)
+    return MLMC_EINVAL;
+  std::memset(st, 0, sizeof(*st));
+  st->eps = eps;
+  st->seed = seed;
+  st->integrator = integrator;
+  st->L = p->level_min;
+  st->phase = 0;
+  return MLMC_OK;
+}
+
+int mlmc_estimate_pass(mlmc_estimate_state* st, const mlmc_params* p, void* workspace,
+                       size_t ws_bytes, void* stream) {
+  return estimate_pass_impl(st, p, workspace, ws_bytes, stream, Shard{0, 1, nullptr, nullptr});
+}
+
+int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, mlmc_result* out) {
+  return estimate_result_impl(st, p, out);
 }
 
 int mlmc_estimate(double eps, int integrator, const mlmc_params* p, uint64_t seed, void* workspace,

@@ -45,7 +45,9 @@ def test_package_import_does_not_need_the_library(monkeypatch):
     import importlib
     import paper_1612_07717_gb300 as M
     monkeypatch.setattr(M, "LIB_PATH", "/nonexistent/libmlmc.so")
-    monkeypatch.setattr(M, "_lib", None)
+    M._lib = None
     with pytest.raises(RuntimeError, match="not built"):
         M.lib()
+    # the reload defines the ctypes classes anew and leaves the library
+    # unloaded, so the next lib() binds its argument types to them
     importlib.reload(M)
