@@ -388,6 +388,25 @@ class Estimation:
         return self.result()
 
 
+def rates(result, level_min=0):
+    """Giles' MLMC rates from an estimate's per-level statistics: alpha with
+    |E[Y_l]| ~ 2^(-alpha l) and beta with V_l ~ 2^(-beta l), least-squares
+    slopes over the coupled levels (level_min + 1 .. L) whose values are
+    positive; None where fewer than two levels qualify."""
+    import math
+
+    def slope(values):
+        pts = [(level_min + k, math.log2(abs(v))) for k, v in enumerate(values)
+               if k > 0 and v != 0.0]
+        if len(pts) < 2:
+            return None
+        mx = sum(x for x, _ in pts) / len(pts)
+        my = sum(y for _, y in pts) / len(pts)
+        sxx = sum((x - mx) ** 2 for x, _ in pts)
+        return -sum((x - mx) * (y - my) for x, y in pts) / sxx
+    return dict(alpha=slope(result["mean_y"]), beta=slope(result["V"]))
+
+
 def torch_allreduce(group=None):
     """A reduce hook for estimate_sharded over a torch.distributed group:
     the buffer goes through a float64 tensor on the group's device (CPU for

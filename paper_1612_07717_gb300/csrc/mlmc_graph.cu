@@ -9,8 +9,18 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mlmc_internal.h"
+
+// NVTX ranges name the host-side phases in a profiler's timeline (a no-op
+// unless a tool is attached).
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace mlmc {
 
@@ -293,6 +303,7 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
 }
 
 int mlmc_graph_launch(mlmc_graph g, void* stream) {
+  NvtxRange nvtx_range("mlmc_graph_launch");
   if (!g) return MLMC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaEventRecord(g->e0, st) != cudaSuccess) return MLMC_ECUDA;

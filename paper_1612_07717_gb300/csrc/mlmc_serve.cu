@@ -28,10 +28,20 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <nvtx3/nvToolsExt.h>
 #include <unordered_map>
 #include <vector>
 
 #include "mlmc_internal.h"
+
+// NVTX ranges name the host-side phases in a profiler's timeline (a no-op
+// unless a tool is attached).
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace mlmc {
 
@@ -517,6 +527,7 @@ int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t
 // issue, wait for the oldest launch first.  Each call folds or launches at
 // least once while any query is active.
 int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active) {
+  NvtxRange nvtx_range("mlmc_server_tick");
   if (!s) return MLMC_EINVAL;
   if (s->failed) return s->failed;  // launches in flight may be lost: do not fold them
   const double t0 = now_s();

@@ -89,3 +89,15 @@ def test_a_complete_state_needs_no_device():
     assert G.lib().mlmc_estimate_pass(C.byref(st), C.byref(p), None, 0, None) == 1
     st.phase = 7
     assert G.lib().mlmc_estimate_pass(C.byref(st), C.byref(p), None, 0, None) == G.EINVAL
+
+
+def test_rates_recover_known_decay():
+    L = 8
+    r = dict(mean_y=[5.0] + [3.0 * 2.0 ** (-1.0 * l) for l in range(1, L + 1)],
+             V=[7.0] + [0.5 * 2.0 ** (-2.0 * l) for l in range(1, L + 1)])
+    got = G.rates(r)
+    assert got["alpha"] == pytest.approx(1.0, abs=1e-12)
+    assert got["beta"] == pytest.approx(2.0, abs=1e-12)
+    # level_min shifts the level index, not the slope; too few levels give None
+    assert G.rates(r, level_min=6)["beta"] == pytest.approx(2.0, abs=1e-12)
+    assert G.rates(dict(mean_y=[1.0, 0.5], V=[1.0, 0.25]))["alpha"] is None

@@ -50,3 +50,12 @@ def test_resume_from_json_gives_the_uninterrupted_result(tmp_path):
     _same(r, ref)
     with open(path) as f:
         assert json.load(f)["phase"] == 2
+
+
+def test_measured_rates_of_an_estimate():
+    # the coupled splitting scheme's variance decays about like h^2 (Section 6.1)
+    p = G.make_params(W.PAPER, precision=G.FP32)
+    r = G.estimate(5e-5, G.BAOAB, p, 3)
+    assert r["L"] - p.level_min >= 3
+    rt = G.rates(r, p.level_min)
+    assert 1.5 < rt["beta"] < 3.0, rt
