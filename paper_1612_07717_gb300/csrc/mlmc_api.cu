@@ -710,6 +710,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       level_spec(hm, q.level, &ls);
       double ppi = std::floor(target / (double)steps_per_pair(ls));
       uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
+      item_paths -= item_paths % min_paths;   // whole passes of the block over its pairs
       if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
       const uint64_t n_it = q.count ? (q.count + item_paths - 1) / item_paths : 0;
       plan[k].lv = ls;

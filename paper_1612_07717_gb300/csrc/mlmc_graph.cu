@@ -51,8 +51,8 @@ __device__ __forceinline__ uint64_t dev_steps(const GState* g, int l) {
 }
 
 // Plan the levels with dN > 0, finest first, exactly as the host planner
-// does: items of about total / (items_per_block * grid) path-steps, at
-// least one block.
+// does: items of about total / (items_per_block * grid) path-steps, in
+// whole passes of a block over its pairs (at least one).
 __device__ void plan_device(const GState* g, DevPlan* plan) {
   double total = 0.0;
   for (int l = g->L; l >= g->lmin; --l)
@@ -67,6 +67,7 @@ __device__ void plan_device(const GState* g, DevPlan* plan) {
       const uint64_t spp = dev_steps(g, l);
       const double ppi = floor(target / (double)spp);
       uint64_t item_paths = ppi < (double)g->min_item ? (uint64_t)g->min_item : (uint64_t)ppi;
+      item_paths -= item_paths % (uint64_t)g->min_item;
       if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
       const uint64_t n_it = (g->dN[l] + item_paths - 1) / item_paths;
       PlanReq& q = plan->req[k++];
