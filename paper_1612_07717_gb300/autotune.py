@@ -1,8 +1,9 @@
 """Autotuner of the persistent multi-level launch.
 
 For each (integrator, precision) it times the batched workload (all levels
-0..12 of the 600 m boundary layer, N_l = n0 * 10^(-l/2)) for every
-combination of
+0..12 of the 600 m boundary layer, N_l = n0 * 10^(-l/2); n0 = 1e9 for FP32 by
+default, the benchmark's own size, since the best item size depends on the
+total work) for every combination of
 
 * kernel variant: one path pair per thread, compiled for 1 (uncapped), 3 or
   4 resident 256-thread blocks per SM, or two pairs per thread on the packed
@@ -11,7 +12,9 @@ combination of
   work items, i.e. how many path pairs one thread integrates per item
   (paths per thread = item paths / 256);
 
-keeps the fastest, and records it as JSON keyed by the GPU name.  ``apply``
+keeps the first combination in sweep order (simpler variant, then fewer
+items) whose rate is within 1 % of the fastest -- closer rates are within
+run-to-run noise -- and records it as JSON keyed by the GPU name.  ``apply``
 loads such a file into the library's tuning table (``mlmc_set_tuning``).
 """
 import ctypes as C
@@ -69,7 +72,14 @@ def _time_launch(integrator, precision, n0, reps=3):
     return steps / (best / 1e3)
 
 
-def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=3e8, verbose=False):
+def select(results, tolerance=0.01):
+    """(rate, variant, items_per_block) of the first entry, in sweep order,
+    within `tolerance` of the best rate."""
+    best = max(r for r, _, _ in results)
+    return next(row for row in results if row[0] >= (1.0 - tolerance) * best)
+
+
+def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=1e9, verbose=False):
     """Sweep the launch knobs; returns {key: best config and rate} and applies the best."""
     out = {}
     for prec in precisions:
@@ -84,7 +94,7 @@ def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=3e8, verbose=False)
                     if verbose:
                         print("integ %d prec %d variant %d items/block %d: %.3e path-steps/s"
                               % (integ, prec, var, ipb, rate), flush=True)
-            rate, var, ipb = max(results)
+            rate, var, ipb = select(results)
             set_tuning(integ, prec, var, ipb, 0)
             out["%d/%d" % (integ, prec)] = dict(variant=var, items_per_block=ipb, blocks_per_sm=0,
                                                 path_steps_per_s=rate,
@@ -96,7 +106,8 @@ def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=3e8, verbose=False)
 
 def save(table, path=DEFAULT_FILE):
     doc = dict(gpu=gpu_name(), when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
-               workload="levels 0..12, N_l = n0 10^(-l/2), BL600 scenario", table=table)
+               workload="levels 0..12, N_l = n0 10^(-l/2), BL600 scenario, "
+               "n0 = 1e9 (FP32), 1e7 (FP64)", table=table)
     with open(path, "w") as f:
         json.dump(doc, f, indent=1)
     return path
