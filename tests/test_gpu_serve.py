@@ -129,3 +129,18 @@ def test_idle_ticks_and_closing_with_launches_in_flight():
     again.run_until_idle()
     assert again.stats()["finished"] == 1
     assert len(ids) == 12
+
+
+def test_fp64_server_and_extreme_slot_counts():
+    qs = [q for q in S.draw_queries(40, seed=3) if round(math.log2(q[2] / q[1]["H"])) == -6][:3]
+    srv = G.Server(precision=G.FP64, max_active=1)          # one slot: strictly one at a time
+    ids = [srv.submit(G.make_params(d, precision=G.FP64), eps) for _, d, eps in qs]
+    srv.run_until_idle()
+    got = [srv.poll(q) for q in ids]
+    for (t, d, eps), r in zip(qs, got):
+        h = G.estimate(eps, G.BAOAB, G.make_params(d, precision=G.FP64), 1)
+        assert h["L"] == r["L"]
+        assert r["estimate"][0] == pytest.approx(h["estimate"][0], rel=1e-9)
+    big = G.Server(max_active=4096)                          # the largest slot table
+    out = _drain(big, qs)
+    assert [r["L"] for r in out] == [r["L"] for r in _drain(G.Server(max_active=2), qs)]
