@@ -51,8 +51,8 @@ __device__ __forceinline__ void adapt_block(const Model<R>& m, const Level<R>& l
         apair_round<INTEG, R, COUPLED>(m, P);
         if (apair_done(P)) {
           apair_finish<R, COUPLED>(P);
-          s_zf[k] = P.f.z;
-          s_zc[k] = P.c.z;
+          s_zf[k] = apair_zf(P);
+          s_zc[k] = apair_zc(P);
           s_info[k] = (P.nf + P.nc) | (P.bad ? 0x80000000u : 0u);
           k = atomicAdd(&s_next, 1u);
           active = k < n;
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(kBlock) k_adapt_paths(const __grid_constant__ 
   APair<R> P;
   run_pair_adapt<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, P);
   R* o = a.states + 4 * j;
-  o[0] = P.f.z; o[1] = P.f.w;
-  o[2] = COUPLED ? P.c.z : R(0);
-  o[3] = COUPLED ? P.c.w : R(0);
+  o[0] = apair_zf(P); o[1] = apair_wf(P);
+  o[2] = COUPLED ? apair_zc(P) : R(0);
+  o[3] = COUPLED ? apair_wc(P) : R(0);
   a.flags[j] = P.bad ? 1 : 0;
   if (a.steps) {
     a.steps[2 * j] = P.nf;

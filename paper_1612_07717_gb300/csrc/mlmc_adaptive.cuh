@@ -26,9 +26,10 @@
 //
 // Work runs in rounds: a round draws one Philox block (four normals) for
 // every lane at once and iterates until the lane has used them; one
-// iteration finishes exactly one step (the fine one first when both end at
-// the same tick), so every lane of a warp runs the same step code whichever
-// path it advances.  A thread runs its pairs back to back (a finished pair
+// iteration finishes exactly one step, that of the path the pair keeps first
+// (the one whose step ends first, the fine one when both end at the same
+// tick), in place, so every lane of a warp runs the same step code whichever
+// path it advances and no path state is copied unless the order changes.  A thread runs its pairs back to back (a finished pair
 // is replaced at the next round), so a lane with short pairs does not wait
 // for a warp-mate's long one; its pairs still enter its sums in index order.
 #pragma once
@@ -104,10 +105,14 @@ __device__ __forceinline__ void astep_finish(const Model<R>& m, APath<R>& p, R S
   reflect_exact(m, p.z, p.w, p.S, bad);
 }
 
-// State of one pair between rounds.
+// State of one pair between rounds: the path that ends its step first
+// (the fine one when both end together) is kept in `a`, the other in `b`,
+// so an iteration steps `a` in place and the pair only swaps when the order
+// changes.
 template <typename R>
 struct APair {
-  APath<R> f, c;
+  APath<R> a, b;
+  bool a_fine;       // a holds the fine path
   uint32_t t;        // current unit (end of the last merged interval)
   uint32_t T_units;  // T in units of h_l / 1024
   uint32_t cap;      // iteration bound of the pair
@@ -118,6 +123,17 @@ struct APair {
   R usec;            // seconds per unit
   bool bad;
 };
+
+template <typename R>
+__device__ __forceinline__ void apair_order(APair<R>& P) {
+  const bool sw = P.b.t_end < P.a.t_end || (P.b.t_end == P.a.t_end && !P.a_fine);
+  if (sw) {
+    const APath<R> x = P.a;
+    P.a = P.b;
+    P.b = x;
+    P.a_fine = !P.a_fine;
+  }
+}
 
 // Start pair i of a level: the shared initial state and the first steps.
 template <typename R, bool COUPLED>
@@ -130,11 +146,13 @@ __device__ __forceinline__ void apair_init(const Model<R>& m, const Level<R>& lv
   P.usec = lv.h * R(0.0009765625);
   R z0, w0;
   initial_state(m, lv, P.i_lo, i_hi, z0, w0);
-  P.f.z = z0; P.f.w = w0; P.f.S = R(1);
-  astep_begin(m, P.f, 1u, 0u, P.T_units, P.usec);
-  P.c = P.f;
-  if (COUPLED) astep_begin(m, P.c, 2u, 0u, P.T_units, P.usec);
-  else P.c.t_end = kNoStep;
+  P.a.z = z0; P.a.w = w0; P.a.S = R(1);
+  astep_begin(m, P.a, 1u, 0u, P.T_units, P.usec);
+  P.b = P.a;
+  if (COUPLED) astep_begin(m, P.b, 2u, 0u, P.T_units, P.usec);
+  else P.b.t_end = kNoStep;
+  P.a_fine = true;
+  apair_order(P);
   // every step is at least one unit: at most T_units steps per path
   P.cap = 2u * P.T_units + 64u;
   P.it = 0;
@@ -147,14 +165,18 @@ __device__ __forceinline__ void apair_init(const Model<R>& m, const Level<R>& lv
 
 template <typename R>
 __device__ __forceinline__ bool apair_done(const APair<R>& P) {
-  return P.bad || (P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end) == kNoStep;
+  return P.bad || P.a.t_end == kNoStep;
 }
+
+template <typename R> __device__ __forceinline__ R apair_zf(const APair<R>& P) { return P.a_fine ? P.a.z : P.b.z; }
+template <typename R> __device__ __forceinline__ R apair_wf(const APair<R>& P) { return P.a_fine ? P.a.w : P.b.w; }
+template <typename R> __device__ __forceinline__ R apair_zc(const APair<R>& P) { return P.a_fine ? P.b.z : P.a.z; }
+template <typename R> __device__ __forceinline__ R apair_wc(const APair<R>& P) { return P.a_fine ? P.b.w : P.a.w; }
 
 // One round: the four normals of Philox block j / 4, then iterations until
 // they are used or the pair is done.  Each iteration adds the merged interval
-// [t, tn] (if not empty) to both paths and finishes exactly one step (the
-// fine one first when both end at tn), so every lane runs the same step
-// code whichever path it advances.
+// [t, tn] (if not empty) to both paths and finishes exactly one step, that of
+// `a` (the fine one first when both end at tn).
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void apair_round(const Model<R>& m, APair<R>& P) {
   const uint4 x = philox10(m.rk0, m.rk1, P.j >> 2, P.i_lo, P.w2, m.stream_id);
@@ -163,30 +185,27 @@ __device__ __forceinline__ void apair_round(const Model<R>& m, APair<R>& P) {
   box_muller(x.z, x.w, x2, x3);
   uint32_t q = 0;
   while (q < 4u) {
-    const uint32_t tn = P.f.t_end < P.c.t_end ? P.f.t_end : P.c.t_end;
+    const uint32_t tn = P.a.t_end;
     if (tn == kNoStep) break;
     if (P.it >= P.cap) { P.bad = true; break; }
     P.it += 1;
-    // the merged interval [t, tn] with xi_j; empty (and a no-op) when the
-    // step just finished ends at the same unit as the other path's
     const bool iv = tn > P.t;
     const R xi = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
     const R d = (R)(tn - P.t) * P.usec;
-    accumulate<INTEG>(P.f, d, xi, iv ? R(1) : R(0));
-    if (COUPLED)
-      accumulate<INTEG>(P.c, d, xi, iv ? (m.coupling ? R(1) : P.f.S) : R(0));  // S_j^(f)
+    const bool fine = P.a_fine;
+    const R Sf = fine ? P.a.S : P.b.S;                              // S_j^(f)
+    const R wc = m.coupling ? R(1) : Sf;
+    accumulate<INTEG>(P.a, d, xi, iv ? (fine ? R(1) : wc) : R(0));
+    if (COUPLED) accumulate<INTEG>(P.b, d, xi, iv ? (fine ? wc : R(1)) : R(0));
     q += iv ? 1u : 0u;
     P.t = tn;
-    const bool fine = P.f.t_end == P.t;
     P.nf += fine ? 1u : 0u;
     P.nc += fine ? 0u : 1u;
-    APath<R> p = fine ? P.f : P.c;
-    const R Sx = (fine || m.coupling) ? R(1) : p.S;                          // S_i^(c)
-    astep_finish<INTEG>(m, p, Sx, P.bad);
-    if (p.t_end == P.T_units) p.t_end = kNoStep;
-    else astep_begin(m, p, fine ? 1u : 2u, P.t, P.T_units, P.usec);
-    if (fine) P.f = p;
-    else P.c = p;
+    const R Sx = (fine || m.coupling) ? R(1) : P.a.S;               // S_i^(c)
+    astep_finish<INTEG>(m, P.a, Sx, P.bad);
+    if (P.a.t_end == P.T_units) P.a.t_end = kNoStep;
+    else astep_begin(m, P.a, fine ? 1u : 2u, P.t, P.T_units, P.usec);
+    if (COUPLED) apair_order(P);
     if (P.bad) break;
   }
   P.j += 4;
@@ -194,8 +213,8 @@ __device__ __forceinline__ void apair_round(const Model<R>& m, APair<R>& P) {
 
 template <typename R, bool COUPLED>
 __device__ __forceinline__ void apair_finish(APair<R>& P) {
-  P.bad |= !(isfinite(P.f.z) && isfinite(P.f.w));
-  if (COUPLED) P.bad |= !(isfinite(P.c.z) && isfinite(P.c.w));
+  P.bad |= !(isfinite(P.a.z) && isfinite(P.a.w));
+  if (COUPLED) P.bad |= !(isfinite(P.b.z) && isfinite(P.b.w));
 }
 
 // One path pair of a level with adaptive timesteps (fine only when not
