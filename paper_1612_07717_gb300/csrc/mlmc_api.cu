@@ -70,9 +70,9 @@ MLMC_DECLARE_MULTI(prec_f32_x2b3)
 struct Tune {
   int variant, items_per_block, blocks_per_sm;
 };
-static Tune g_tune[3][2] = {{{3, 16, 0}, {1, 16, 0}},   // SE
-                            {{3, 16, 0}, {1, 16, 0}},   // GL
-                            {{4, 16, 0}, {1, 16, 0}}};  // BAOAB
+static Tune g_tune[3][2] = {{{1, 8, 0}, {1, 4, 0}},     // SE
+                            {{13, 16, 0}, {1, 16, 0}},  // GL
+                            {{13, 32, 0}, {1, 16, 0}}}; // BAOAB
 static std::mutex g_tune_mu;
 
 static Tune tune_of(int prec, int integ) {
@@ -85,10 +85,10 @@ uint64_t min_item_paths(int prec, int integ) {
   return (uint64_t)kBlock * (tune_of(prec, integ).variant >= 12 ? 2u : 1u);
 }
 
-#define MLMC_DISPATCH_MULTI(prec, integ, CALL)                     \
+#define MLMC_DISPATCH_VARIANT(prec, variant, CALL)                 \
   do {                                                             \
     if (prec) return prec_f64::CALL;                               \
-    switch (tune_of(prec, integ).variant) {                        \
+    switch (variant) {                                             \
       case 3: return prec_f32_b3::CALL;                            \
       case 4: return prec_f32_b4::CALL;                            \
       case 12: return prec_f32_x2::CALL;                           \
@@ -96,6 +96,8 @@ uint64_t min_item_paths(int prec, int integ) {
       default: return prec_f32::CALL;                              \
     }                                                              \
   } while (0)
+#define MLMC_DISPATCH_MULTI(prec, integ, CALL) \
+  MLMC_DISPATCH_VARIANT(prec, tune_of(prec, integ).variant, CALL)
 
 cudaError_t launch_level_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                               uint64_t N, uint64_t offset, Partial* partials, int grid,
@@ -126,6 +128,16 @@ cudaError_t launch_multilevel_table(int prec, int integ, const void* models, siz
 }
 static int occupancy_multi(int prec, int integ) {
   MLMC_DISPATCH_MULTI(prec, integ, occupancy_multi(integ));
+}
+cudaError_t launch_multilevel_table_variant(int variant, int prec, int integ, const void* models,
+                                            size_t stride, const PlanReq* reqs, int n_req,
+                                            uint32_t n_items, Partial* partials,
+                                            unsigned int* counter, int grid, cudaStream_t st) {
+  MLMC_DISPATCH_VARIANT(prec, variant, multilevel_table(integ, models, stride, reqs, n_req,
+                                                        n_items, partials, counter, grid, st));
+}
+static int occupancy_variant(int variant, int prec, int integ) {
+  MLMC_DISPATCH_VARIANT(prec, variant, occupancy_multi(integ));
 }
 static int occupancy_sums(int prec, int integ) {
   MLMC_DISPATCH_MULTI(prec, integ, occupancy_sums(integ));
@@ -479,6 +491,14 @@ int grid_for(int prec, int integ, bool multilevel, uint64_t N) {
     const uint64_t need = (N + per_block - 1) / per_block;
     if (need < (uint64_t)g) g = (int)(need > 0 ? need : 1);
   }
+  return g;
+}
+
+int grid_for_variant(int variant, int prec, int integ) {
+  DevInfo di;
+  if (device_info(&di) != MLMC_OK) return 0;
+  int g = di.sms * occupancy_variant(variant, prec, integ);
+  if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
   return g;
 }
 

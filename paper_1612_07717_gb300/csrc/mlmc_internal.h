@@ -122,6 +122,15 @@ int items_per_block(int prec, int integ);
 // Smallest work item of the planners: one pass of the block over its path
 // pairs (kBlock pairs, 2 kBlock for the two-pairs-per-thread variants).
 uint64_t min_item_paths(int prec, int integ);
+// The query server's kernel, whatever the tuning table holds: one path pair
+// per thread at 4 blocks per SM, the finest work items (latency before
+// throughput); its launcher and grid.
+constexpr int kServeVariant = 4;
+cudaError_t launch_multilevel_table_variant(int variant, int prec, int integ, const void* models,
+                                            size_t stride, const PlanReq* reqs, int n_req,
+                                            uint32_t n_items, Partial* partials,
+                                            unsigned int* counter, int grid, cudaStream_t st);
+int grid_for_variant(int variant, int prec, int integ);
 
 // Device facts, workspace carving and parameter handling (mlmc_api.cu).
 struct DevInfo {

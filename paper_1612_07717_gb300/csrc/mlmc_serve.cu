@@ -345,7 +345,7 @@ static void admit(mlmc_server_s* s) {
 static int issue(mlmc_server_s* s, bool* launched) {
   *launched = false;
   if (s->idle.empty()) return MLMC_OK;
-  const uint64_t min_item = min_item_paths(s->prec, s->integ);
+  const uint64_t min_item = kBlock;  // one pass of a block: one pair per thread
   std::vector<std::pair<double, size_t>> order;
   for (size_t k = 0; k < s->active.size(); ++k) {
     const Query& qq = s->q[s->active[k]];
@@ -416,9 +416,10 @@ static int issue(mlmc_server_s* s, bool* launched) {
   if (!rc) rc = cuda_status(cudaMemcpyAsync(f.d_reqs, f.h_reqs, n_req * sizeof(PlanReq),
                                             cudaMemcpyHostToDevice, f.st));
   if (!rc) rc = cuda_status(cudaMemsetAsync(f.d_counter, 0, sizeof(unsigned int), f.st));
-  if (!rc) rc = cuda_status(launch_multilevel_table(s->prec, s->integ, s->d_models, kModelSlot,
-                                                    f.d_reqs, n_req, (uint32_t)items, f.d_partials,
-                                                    f.d_counter, s->grid, f.st));
+  if (!rc) rc = cuda_status(launch_multilevel_table_variant(kServeVariant, s->prec, s->integ,
+                                                            s->d_models, kModelSlot, f.d_reqs,
+                                                            n_req, (uint32_t)items, f.d_partials,
+                                                            f.d_counter, s->grid, f.st));
   if (!rc) rc = cuda_status(launch_finalize_table(f.d_partials, f.d_reqs, n_req, f.d_results, f.st));
   if (!rc) rc = cuda_status(cudaMemcpyAsync(f.h_results, f.d_results,
                                             n_req * sizeof(mlmc_level_result),
@@ -445,7 +446,7 @@ int mlmc_server_create(int integrator, int precision, int max_active, uint64_t s
   if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < server_bytes(max_active))
     return MLMC_EWORKSPACE;
   if (model_bytes(precision) > kModelSlot) return MLMC_EINVAL;
-  const int grid = grid_for(precision, integrator, true, 0);
+  const int grid = grid_for_variant(kServeVariant, precision, integrator);
   if (grid <= 0) return MLMC_ENODEV;
   mlmc_server_s* s = new mlmc_server_s();
   s->integ = integrator;
