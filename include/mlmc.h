@@ -393,7 +393,9 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  *   mlmc_server_tick     folds the launches that have completed (oldest
  *                        first), admits queued queries while a slot is
  *                        free, and puts one more launch in flight (at most
- *                        four): one persistent launch over chunks (at most
+ *                        four): one persistent launch (of the one-pair
+ *                        kernel, variant 4, whatever the tuning table
+ *                        holds: the finest work items) over chunks (at most
  *                        2^26 path-steps each) of the active queries'
  *                        pending passes -- least pending work first, a
  *                        waiting query's priority doubling every launch --
