@@ -455,8 +455,12 @@ static int path_adaptive(const orc_params* p, int integ, int level, uint64_t i, 
   return 0;
 }
 
-int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t seed,
-             orc_path_out* out, double* trace_f, double* trace_c) {
+/* The uniform-timestep pair of orc_path; for BAOAB, half_f (3 * M doubles)
+ * and half_c (3 * M/2) optionally receive (z, w, S) after the first half of
+ * every step, i.e. after the fold that follows its first A half-step. */
+static int path_pair(const orc_params* pin, int integ, int level, uint64_t i, uint64_t seed,
+                     orc_path_out* out, double* trace_f, double* trace_c, double* half_f,
+                     double* half_c) {
   orc_params pp = *pin;
   orc_params* p = &pp;
   if (orc_normalise(p) != 0) return -1;
@@ -467,9 +471,10 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
   const int coupled = level > p->level_min;
   if (coupled && (M % 2) != 0) return -1;
   if (p->z_adapt > 0.0) {
-    if (trace_f || trace_c) return -1;
+    if (trace_f || trace_c || half_f || half_c) return -1;
     return path_adaptive(p, integ, level, i, seed, out);
   }
+  if ((half_f || half_c) && integ != ORC_BAOAB) return -1;
   const double h = p->T / (double)M;
 
   state_t f, c;
@@ -489,6 +494,7 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
     for (int64_t n = 0; n < M && !f.bad; ++n) {
       double xi = NORMAL(n);
       coef_t co = step_pre(integ, p, &f, h);
+      trace_put(half_f, (int)n, &f);
       step_post(integ, p, &f, h, xi, &co);
       trace_put(trace_f, (int)(n + 1), &f);
     }
@@ -501,16 +507,19 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
       double xb = NORMAL(2 * k + 1);
       /* fine sub-step 2k */
       coef_t ca = step_pre(integ, p, &f, h);
+      trace_put(half_f, (int)(2 * k), &f);
       int Sa = f.S;            /* S_n^{(f)} at the time xi_n is applied */
       step_post(integ, p, &f, h, xa, &ca);
       trace_put(trace_f, (int)(2 * k + 1), &f);
       /* fine sub-step 2k+1 */
       coef_t cb = step_pre(integ, p, &f, h);
+      trace_put(half_f, (int)(2 * k + 1), &f);
       int Sb = f.S;            /* S_{n+1}^{(f)} */
       step_post(integ, p, &f, h, xb, &cb);
       trace_put(trace_f, (int)(2 * k + 2), &f);
       /* coarse step k with timestep 2h */
       coef_t cc = step_pre(integ, p, &c, 2.0 * h);
+      trace_put(half_c, (int)k, &c);
       int Sc = c.S;            /* S_n^{(c)} */
       if (p->coupling == 1) { Sa = 1; Sb = 1; Sc = 1; }  /* naive coupling */
       double xc;
@@ -538,6 +547,16 @@ int orc_path(const orc_params* pin, int integ, int level, uint64_t i, uint64_t s
   out->tie = 1.0;
   out->gap = 1.0;
   return 0;
+}
+
+int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
+             orc_path_out* out, double* trace_f, double* trace_c) {
+  return path_pair(p, integ, level, i, seed, out, trace_f, trace_c, NULL, NULL);
+}
+
+int orc_path_half(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
+                  orc_path_out* out, double* half_f, double* half_c) {
+  return path_pair(p, integ, level, i, seed, out, NULL, NULL, half_f, half_c);
 }
 
 /* ------------------------------------------------------------------------ */

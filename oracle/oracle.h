@@ -126,6 +126,15 @@ int orc_normalise(orc_params* p);
 int orc_path(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
              orc_path_out* out, double* trace_f, double* trace_c);
 
+/* orc_path for BAOAB with uniform timesteps, recording (z, w, S) after the
+ * first half of every step -- the state after the fold that follows the
+ * first A half-step (Eq. MethodBAOAB), where the noise of the step enters --
+ * into half_f (3 * M doubles, row n for fine step n) and, on coupled levels,
+ * half_c (3 * M/2 doubles); either may be NULL.  Returns -1 for another
+ * integrator, adaptive timesteps or bad arguments. */
+int orc_path_half(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
+                  orc_path_out* out, double* half_f, double* half_c);
+
 /* Level sums over paths [offset, offset + N).  threads <= 0 uses 1.  The
  * result does not depend on the thread count. */
 int orc_level_sums(const orc_params* p, int integ, int level, uint64_t N,

@@ -69,6 +69,8 @@ def lib():
         L.orc_normalise.argtypes = [C.POINTER(Params)]
         L.orc_path.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                C.POINTER(PathOut), C.c_void_p, C.c_void_p]
+        L.orc_path_half.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                    C.POINTER(PathOut), C.c_void_p, C.c_void_p]
         L.orc_level_sums.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_uint64,
                                      C.c_uint64, C.c_uint64, C.c_int, C.POINTER(LevelSums)]
         L.orc_smooth_poly.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -144,6 +146,22 @@ def path(p, integ, level, i, seed, trace=False):
         out["trace_f"] = tf
         out["trace_c"] = tc
     return out
+
+
+def path_half(p, integ, level, i, seed):
+    """BAOAB pair with the (z, w, S) rows after the first half of every step
+    (the fold that follows the first A half-step): half_f (M rows) and
+    half_c (M/2 rows; zeros on the coarsest level)."""
+    r = PathOut()
+    M = p.M0 << level
+    hf = np.zeros((M, 3))
+    hc = np.zeros((M // 2, 3))
+    rc = lib().orc_path_half(C.byref(p), integ, level, i, seed, C.byref(r), hf.ctypes.data,
+                             hc.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_path_half rejected its arguments")
+    return dict(zf=r.zf, wf=r.wf, zc=r.zc, wc=r.wc, nonfinite=r.nonfinite, half_f=hf,
+                half_c=hc)
 
 
 def paths(p, integ, level, N, offset, seed, extra=False):

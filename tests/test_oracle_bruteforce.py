@@ -75,9 +75,10 @@ def fold(p, X, U, S):
     return X, U, S
 
 
-def step(p, integ, st, h, get_xi):
+def step(p, integ, st, h, get_xi, half=None):
     """One step; get_xi(S, lam) returns the normal given the parity and the
-    O-step lambda at the noise time."""
+    O-step lambda at the noise time; half (a list) receives BAOAB's state
+    after its first half-step."""
     X, U, S = st
     if integ == 0:
         c = coef(p, X)
@@ -97,6 +98,8 @@ def step(p, integ, st, h, get_xi):
     U = U - dvdx(c, U) * h / 2
     X = X + U * h / 2
     X, U, S = fold(p, X, U, S)
+    if half is not None:
+        half.append((X, U, S))
     c = coef(p, X)
     xi = get_xi(S, c[1])
     e = math.exp(-c[1] * h)
@@ -108,8 +111,9 @@ def step(p, integ, st, h, get_xi):
     return X, U, S
 
 
-def pair(p, integ, level, i, seed):
+def pair(p, integ, level, i, seed, halves=None):
     M = p["M0"] << level
+    hf, hc = ([], []) if halves is None else halves
     h = p["T"] / M
     x = words(p, level, i, 0xFFFFFFFF, seed)
     X0, U0 = p["z0"], p["w0"]
@@ -133,9 +137,9 @@ def pair(p, integ, level, i, seed):
                 rec[n] = (S, lam)
                 return xi[n]
             return get
-        f = step(p, integ, f, h, g(2 * k))
+        f = step(p, integ, f, h, g(2 * k), hf)
         tf.append(f)
-        f = step(p, integ, f, h, g(2 * k + 1))
+        f = step(p, integ, f, h, g(2 * k + 1), hf)
         tf.append(f)
         (Sa, lam_a), (Sb, _) = rec[2 * k], rec[2 * k + 1]
 
@@ -145,7 +149,7 @@ def pair(p, integ, level, i, seed):
                 return Sc / math.sqrt(2) * (sa * xi[2 * k] + sb * xi[2 * k + 1])
             e = math.exp(-lam_a * h)
             return Sc * (e * sa * xi[2 * k] + sb * xi[2 * k + 1]) / math.sqrt(e * e + 1)
-        c = step(p, integ, c, 2 * h, gc)
+        c = step(p, integ, c, 2 * h, gc, hc)
         tc.append(c)
     return np.array(tf), np.array(tc)
 
@@ -173,3 +177,23 @@ def test_oracle_trace_equals_python_restatement(case, integ):
         tf, tc = pair(d, integ, level, i + 1000, 123456789012)
         assert np.allclose(r["trace_f"], tf, rtol=1e-11, atol=1e-12 * d["H"]), i
         assert np.allclose(r["trace_c"], tc, rtol=1e-11, atol=1e-12 * d["H"]), i
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_oracle_baoab_half_steps_equal_python_restatement(case):
+    # the rows after the first half of each BAOAB step (the fold after the
+    # first A half-step, where the step's noise enters)
+    d, level = CASES[case]
+    d = dict(d)
+    d.setdefault("uniform_map", 1)
+    p = O.make_params(d)
+    d["H"] = p.H
+    for i in range(8):
+        r = O.path_half(p, 2, level, i + 1000, 123456789012)
+        hf, hc = [], []
+        tf, tc = pair(d, 2, level, i + 1000, 123456789012, (hf, hc))
+        assert np.allclose(r["half_f"], np.array(hf), rtol=1e-11, atol=1e-12 * d["H"]), i
+        assert np.allclose(r["half_c"], np.array(hc), rtol=1e-11, atol=1e-12 * d["H"]), i
+        assert r["zf"] == pytest.approx(tf[-1][0], rel=1e-11, abs=1e-12 * d["H"])
+    with pytest.raises(ValueError):
+        O.path_half(p, 1, level, 0, 1)
