@@ -233,13 +233,18 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
  * Instead of a caller workspace it uses one array of device memory that the
  * library defines statically: 256 + 4096 * 128 bytes (about 0.5 MiB), held
  * on every GPU that loads the library until the process exits.  The work is
- * split into at most 4096 items (items are enlarged to fit); a batch that
- * cannot be split that way (more than 4096 * (2^31 - 1) pairs) returns
- * MLMC_EWORKSPACE, more than 32 requests MLMC_EINVAL.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * split into the same items as mlmc_multilevel_sums_async uses whenever that
+ * split has at most 4096 items (the sums are then bit-identical); a larger
+ * split gets larger items until it fits; a batch that cannot be split that
+ * way (more than 4096 * (2^31 - 1) pairs) returns MLMC_EWORKSPACE, more than
+ * 32 requests MLMC_EINVAL.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  *
- * The first call on each device looks up the array's device address once
- * (cudaGetSymbolAddress, with that device current); make that first call
+ * The first call in each CUDA context (normally a device's primary context)
+ * looks up the array's device address once (cudaGetSymbolAddress, with that
+ * context current; with no context current it creates the primary one) and
+ * keeps it under the context's unique id, so a call after cudaDeviceReset or
+ * in another context looks it up again; make the first call in a context
  * before any stream capture begins.  All calls share the one array and it
  * keeps the last call's contents: the call clears the work counter itself,
  * but two calls that overlap on the GPU (different streams, no ordering
@@ -329,8 +334,10 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
  * the sums, applies N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)),
  * the bias test and the next plan, and sets the loop condition.  The driver
  * state, plan and result live in the workspace (which must stay alive and
- * unused by other calls while the graph runs).  The loop is bounded: at most
- * 4 * MLMC_MAX_LEVELS passes, else MLMC_ETIMEOUT.
+ * unused by other calls while the graph runs).  The loop is bounded: after
+ * its pass limit (4 * MLMC_MAX_LEVELS passes; mlmc_graph_create_ex sets a
+ * smaller one) a pass that would start another one ends the loop instead,
+ * and mlmc_graph_result returns MLMC_ETIMEOUT with the partial result.
  *   mlmc_graph_create   builds and instantiates the graph (host work; no
  *                       kernel runs yet); returns an opaque handle
  *   mlmc_graph_launch   enqueues one complete estimate on `stream`
@@ -343,6 +350,13 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
 typedef struct mlmc_graph_s* mlmc_graph;
 int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
                       void* workspace, size_t ws_bytes, mlmc_graph* out);
+/* mlmc_graph_create with the device loop's pass limit: max_passes launches of
+ * the persistent kernel at most (1..4 * MLMC_MAX_LEVELS; 0 = that default),
+ * after which the update kernel ends the loop with MLMC_ETIMEOUT.  A watchdog
+ * on the device-side loop, settable from the host; the paper has no
+ * counterpart. */
+int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                         int max_passes, void* workspace, size_t ws_bytes, mlmc_graph* out);
 int mlmc_graph_launch(mlmc_graph g, void* stream);
 int mlmc_graph_result(mlmc_graph g, void* stream, mlmc_result* out);
 int mlmc_graph_destroy(mlmc_graph g);
@@ -439,6 +453,24 @@ int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_par
                            uint64_t seed, uint64_t path_offset, void* d_states,
                            int32_t* d_flags, void* stream);
 
+/* mlmc_level_paths_async through the path code of one tuning variant of the
+ * level-sums and persistent multi-level kernels (see mlmc_set_tuning):
+ * variant 0 = the variant the tuning table names for (integrator,
+ * precision); 1, 3, 4 = one pair per thread at that register budget; 12, 13
+ * = two pairs per thread on the packed FP32 instructions (thread g takes
+ * pairs 2g and 2g + 1; for an odd N the last lane is computed and
+ * discarded), the code the batched launches reduce.  Every variant gives the
+ * same paths bit for bit; this entry point lets a caller check that, and
+ * check the batched kernels pair by pair.  Same outputs and layout as
+ * mlmc_level_paths_async; MLMC_EINVAL for another variant, or a packed one
+ * with FP64 paths.  With adaptive timesteps every variant runs the one
+ * adaptive kernel.  No synchronisation.  Paths as Section 3.3 (Eqs.
+ * MethodSymplecticEuler, MethodSymplecticEulerOU, MethodBAOAB and the coupled
+ * increments of Eqs. euler_coupled_treatment, splitting_coupled_treatment). */
+int mlmc_level_paths_variant_async(int variant, int level, uint64_t N, int integrator,
+                                   const mlmc_params* p, uint64_t seed, uint64_t path_offset,
+                                   void* d_states, int32_t* d_flags, void* stream);
+
 /* mlmc_level_paths_async for adaptive timesteps (p->z_adapt > 0, else
  * MLMC_EINVAL), also writing the integrator steps of each pair: d_steps gets
  * N x 2 int64 values (fine, coarse; coarse 0 on level_min).  No
@@ -453,6 +485,18 @@ int mlmc_level_paths_steps_async(int level, uint64_t N, int integrator, const ml
 int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_params* p,
                           uint64_t seed, uint64_t path_offset, void* d_trace_f,
                           void* d_trace_c, void* stream);
+
+/* BAOAB's state after the first half of every step (Eq. MethodBAOAB: after
+ * the B and A half-steps and the fold that follows, where the step's noise
+ * enters): d_half_f gets N x M x 3 values (z, w, S; row n for fine step n),
+ * d_half_c N x M/2 x 3 (may be NULL on level_min).  Together with
+ * mlmc_path_trace_async it locates every fold of a path; a reflection whose
+ * order FP32 and FP64 paths disagree on shows here even when the full-step
+ * parities agree again.  BAOAB with uniform timesteps only (else
+ * MLMC_EINVAL).  No synchronisation. */
+int mlmc_path_trace_half_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                               uint64_t seed, uint64_t path_offset, void* d_half_f,
+                               void* d_half_c, void* stream);
 
 /* ------------------------------------------------------------ measurement */
 /* The paper has no counterpart: this measures the roofline denominator of

@@ -121,6 +121,8 @@ def lib():
                                             C.POINTER(Result)]
         L.mlmc_graph_create.argtypes = [C.c_double, i32, C.POINTER(Params), u64, vp, C.c_size_t,
                                         C.POINTER(vp)]
+        L.mlmc_graph_create_ex.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, vp,
+                                           C.c_size_t, C.POINTER(vp)]
         L.mlmc_graph_launch.argtypes = [vp, vp]
         L.mlmc_graph_result.argtypes = [vp, vp, C.POINTER(Result)]
         L.mlmc_graph_destroy.argtypes = [vp]
@@ -146,9 +148,13 @@ def lib():
         L.mlmc_stmc_estimate.argtypes = [C.c_double, i32, i32, i32, C.POINTER(Params), u64, vp,
                                          C.c_size_t, vp, C.POINTER(Result)]
         L.mlmc_level_paths_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
+        L.mlmc_level_paths_variant_async.argtypes = [i32, i32, u64, i32, C.POINTER(Params), u64,
+                                                     u64, vp, vp, vp]
         L.mlmc_level_paths_steps_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp,
                                                    vp, vp, vp]
         L.mlmc_path_trace_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp, vp, vp]
+        L.mlmc_path_trace_half_async.argtypes = [i32, u64, i32, C.POINTER(Params), u64, u64, vp,
+                                                 vp, vp]
         _lib = L
     return _lib
 
@@ -463,15 +469,16 @@ def estimate_graph(eps, integrator, params, seed, workspace=None, stream=None):
 
 
 class GraphEstimator:
-    """An instantiated graph of the adaptive loop, launched many times."""
+    """An instantiated graph of the adaptive loop, launched many times;
+    max_passes > 0 lowers the device loop's pass limit (its watchdog)."""
 
-    def __init__(self, eps, integrator, params, seed, workspace=None):
+    def __init__(self, eps, integrator, params, seed, workspace=None, max_passes=0):
         self.params = params
         self.ws = workspace or Workspace(params)
         self.handle = C.c_void_p()
-        rc = lib().mlmc_graph_create(eps, integrator, C.byref(params), seed, *self.ws.args(),
-                                     C.byref(self.handle))
-        _check(rc, "mlmc_graph_create")
+        rc = lib().mlmc_graph_create_ex(eps, integrator, C.byref(params), seed, max_passes,
+                                        *self.ws.args(), C.byref(self.handle))
+        _check(rc, "mlmc_graph_create_ex")
 
     def launch(self, stream=None):
         _check(lib().mlmc_graph_launch(self.handle, _stream_handle(stream)), "mlmc_graph_launch")
@@ -537,13 +544,22 @@ def stmc_estimate(eps, level, integrator, params, seed, n_pilot=10000, workspace
     return out
 
 
-def level_paths(level, N, integrator, params, seed, path_offset=0, stream=None, steps=False):
+def level_paths(level, N, integrator, params, seed, path_offset=0, stream=None, steps=False,
+                variant=None):
     """Final (z_f, w_f, z_c, w_c) of N pairs as an (N, 4) CUDA tensor, plus flags;
-    with steps=True (adaptive timesteps only) also the (N, 2) int64 step counts."""
+    with steps=True (adaptive timesteps only) also the (N, 2) int64 step counts;
+    with variant (0 = the tuning table's, or 1, 3, 4, 12, 13) through that
+    tuning variant's path code (``mlmc_level_paths_variant_async``)."""
     import torch
     dt = torch.float64 if params.precision == FP64 else torch.float32
     states = torch.empty((N, 4), dtype=dt, device="cuda")
     flags = torch.empty(N, dtype=torch.int32, device="cuda")
+    if variant is not None:
+        rc = lib().mlmc_level_paths_variant_async(
+            variant, level, N, integrator, C.byref(params), seed, path_offset,
+            C.c_void_p(states.data_ptr()), C.c_void_p(flags.data_ptr()), _stream_handle(stream))
+        _check(rc, "mlmc_level_paths_variant_async")
+        return states, flags
     if steps:
         st = torch.empty((N, 2), dtype=torch.int64, device="cuda")
         rc = lib().mlmc_level_paths_steps_async(
@@ -571,6 +587,21 @@ def path_trace(level, N, integrator, params, seed, path_offset=0, stream=None):
                                      _stream_handle(stream))
     _check(rc, "mlmc_path_trace_async")
     return tf, tc
+
+
+def path_trace_half(level, N, integrator, params, seed, path_offset=0, stream=None):
+    """BAOAB's (z, w, S) after the first half of every step: (N, M, 3) fine and
+    (N, M/2, 3) coarse CUDA tensors (``mlmc_path_trace_half_async``)."""
+    import torch
+    dt = torch.float64 if params.precision == FP64 else torch.float32
+    M = params.M0 << level
+    hf = torch.zeros((N, M, 3), dtype=dt, device="cuda")
+    hc = torch.zeros((N, M // 2, 3), dtype=dt, device="cuda")
+    rc = lib().mlmc_path_trace_half_async(level, N, integrator, C.byref(params), seed, path_offset,
+                                          C.c_void_p(hf.data_ptr()), C.c_void_p(hc.data_ptr()),
+                                          _stream_handle(stream))
+    _check(rc, "mlmc_path_trace_half_async")
+    return hf, hc
 
 
 class Server:

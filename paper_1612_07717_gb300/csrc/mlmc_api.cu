@@ -37,6 +37,8 @@ namespace mlmc {
   int occupancy_sums(int);                                                                     \
   cudaError_t level_sums(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t,         \
                          Partial*, int, cudaStream_t);                                          \
+  cudaError_t paths_variant(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t,      \
+                            void*, int32_t*, cudaStream_t);                                     \
   }
 #define MLMC_DECLARE_ALL(NS)                                                                   \
   MLMC_DECLARE_MULTI(NS)                                                                       \
@@ -44,7 +46,7 @@ namespace mlmc {
   size_t model_size();                                                                         \
   void model_image(const HostModel&, void*);                                                   \
   cudaError_t paths(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, void*,       \
-                    int32_t*, void*, void*, bool, cudaStream_t);                                \
+                    int32_t*, void*, void*, void*, void*, bool, cudaStream_t);                  \
   int occupancy(int, bool);                                                                    \
   cudaError_t pdf(int, const HostModel&, const LevelSpec&, uint64_t, uint64_t, int, double*,  \
                   int, cudaStream_t);                                                           \
@@ -150,13 +152,26 @@ void model_image(int prec, const HostModel& hm, void* out) {
 cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                          uint64_t offset, void* s, int32_t* f, cudaStream_t st) {
   if (hm.adapt) return launch_adapt_paths(prec, integ, hm, lv, N, offset, s, f, nullptr, st);
-  return prec ? prec_f64::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st)
-              : prec_f32::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, false, st);
+  return prec ? prec_f64::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, nullptr, nullptr,
+                                false, st)
+              : prec_f32::paths(integ, hm, lv, N, offset, s, f, nullptr, nullptr, nullptr, nullptr,
+                                false, st);
+}
+// Final states through the path code of one tuning variant (variant 0: the
+// table's variant for this integrator and precision).
+static cudaError_t launch_paths_variant(int variant, int prec, int integ, const HostModel& hm,
+                                        const LevelSpec& lv, uint64_t N, uint64_t offset, void* s,
+                                        int32_t* f, cudaStream_t st) {
+  if (variant == 0) variant = tune_of(prec, integ).variant;
+  MLMC_DISPATCH_VARIANT(prec, variant, paths_variant(integ, hm, lv, N, offset, s, f, st));
 }
 cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
-                         uint64_t offset, void* tf, void* tc, cudaStream_t st) {
-  return prec ? prec_f64::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st)
-              : prec_f32::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, true, st);
+                         uint64_t offset, void* tf, void* tc, void* thf, void* thc,
+                         cudaStream_t st) {
+  return prec ? prec_f64::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, thf, thc, true,
+                                st)
+              : prec_f32::paths(integ, hm, lv, N, offset, nullptr, nullptr, tf, tc, thf, thc, true,
+                                st);
 }
 cudaError_t launch_pdf(int prec, int integ, const HostModel& hm, const LevelSpec& lv, uint64_t N,
                        uint64_t offset, int k, double* partials, int grid, cudaStream_t st) {
@@ -696,10 +711,15 @@ int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
 }
 
 // Plan a multi-level launch: requests sorted by per-pair cost (finest level
-// first), split into items of about `target` path-steps.
+// first), split into items of about total / (items_per_block * grid)
+// path-steps, each a whole number of block passes over its pairs; the item
+// size doubles until the plan has at most max_items items.  Items are capped
+// at 2^31 - 1 pairs; a batch that still needs more than max_items items
+// returns too_many_rc.  Both batched forms (workspace and allocation-free)
+// plan with this function, so a batch that fits both gets the same items.
 static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
-                         const mlmc_params* p, int grid, ReqPlan* plan, int* order,
-                         uint32_t* n_items_out) {
+                         const mlmc_params* p, int grid, uint32_t max_items, int too_many_rc,
+                         ReqPlan* plan, int* order, uint32_t* n_items_out) {
   if (!reqs || n_req < 1 || n_req > kMaxReq) return MLMC_EINVAL;
   double total = 0.0;
   for (int r = 0; r < n_req; ++r) {
@@ -716,14 +736,14 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
     while (j >= 0 && reqs[order[j]].level < reqs[v].level) { order[j + 1] = order[j]; --j; }
     order[j + 1] = v;
   }
-  // about items_per_block items per resident block, bounded by kMaxItems
+  // about items_per_block items per resident block
   double target = total / ((double)items_per_block(p->precision, integ) * (double)grid);
   if (target < 1.0) target = 1.0;
   // the adaptive kernels run one pair per thread at a time
   const uint64_t min_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
-  uint64_t items = 0;
-  for (int pass = 0; pass < 40; ++pass) {
-    items = 0;
+  for (int pass = 0; pass < 64; ++pass) {
+    uint64_t items = 0;
+    bool capped = false;
     for (int k = 0; k < n_req; ++k) {
       const mlmc_level_request& q = reqs[order[k]];
       LevelSpec ls;
@@ -731,7 +751,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       double ppi = std::floor(target / (double)steps_per_pair(ls));
       uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
       item_paths -= item_paths % min_paths;   // whole passes of the block over its pairs
-      if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
+      if (item_paths > 0x7FFFFFFFull) { item_paths = 0x7FFFFFFFull; capped = true; }
       const uint64_t n_it = q.count ? (q.count + item_paths - 1) / item_paths : 0;
       plan[k].lv = ls;
       plan[k].first = q.first;
@@ -742,12 +762,14 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       plan[k].path_steps = fixed_steps(hm, ls, q.count);
       items += n_it;
     }
-    if (items <= (uint64_t)kMaxItems) break;
+    if (items <= (uint64_t)max_items) {
+      *n_items_out = (uint32_t)items;
+      return MLMC_OK;
+    }
+    if (capped) break;
     target *= 2.0;
   }
-  if (items > (uint64_t)kMaxItems) return MLMC_EINVAL;
-  *n_items_out = (uint32_t)items;
-  return MLMC_OK;
+  return too_many_rc;
 }
 
 static int multilevel_launch(const mlmc_level_request* reqs, int n_req, int integrator,
@@ -764,7 +786,9 @@ static int multilevel_launch(const mlmc_level_request* reqs, int n_req, int inte
   const int grid = grid_for(prec, integrator, true, 0);
   if (grid <= 0) return MLMC_ENODEV;
   uint32_t n_items = 0;
-  if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, plan, order, &n_items))) return rc;
+  if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, (uint32_t)kMaxItems, MLMC_EINVAL,
+                          plan, order, &n_items)))
+    return rc;
   rc = cuda_status(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), st));
   if (rc) return rc;
   rc = cuda_status(launch_multilevel(prec, integrator, hm, plan, n_req, n_items, w.partials,
@@ -1092,6 +1116,30 @@ int mlmc_level_paths_async(int level, uint64_t N, int integrator, const mlmc_par
                                   d_flags, (cudaStream_t)stream));
 }
 
+int mlmc_level_paths_variant_async(int variant, int level, uint64_t N, int integrator,
+                                   const mlmc_params* p, uint64_t seed, uint64_t path_offset,
+                                   void* d_states, int32_t* d_flags, void* stream) {
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  if (variant != 0 && variant != 1 && variant != 3 && variant != 4 && variant != 12 &&
+      variant != 13)
+    return MLMC_EINVAL;
+  if (N && (!d_states || !d_flags)) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  if (p->precision == MLMC_FP64 && variant > 1) return MLMC_EINVAL;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (hm.adapt) {   // one adaptive kernel serves every variant
+    return cuda_status(launch_adapt_paths(p->precision, integrator, hm, ls, N, path_offset,
+                                          d_states, d_flags, nullptr, st));
+  }
+  return cuda_status(launch_paths_variant(variant, p->precision, integrator, hm, ls, N,
+                                          path_offset, d_states, d_flags, st));
+}
+
 int mlmc_level_paths_steps_async(int level, uint64_t N, int integrator, const mlmc_params* p,
                                  uint64_t seed, uint64_t path_offset, void* d_states,
                                  int32_t* d_flags, int64_t* d_steps, void* stream) {
@@ -1147,7 +1195,23 @@ int mlmc_path_trace_async(int level, uint64_t N, int integrator, const mlmc_para
   if ((rc = level_spec(hm, level, &ls))) return rc;
   if ((rc = check_stable(integrator, p, hm, ls))) return rc;
   return cuda_status(launch_trace(p->precision, integrator, hm, ls, N, path_offset, d_trace_f,
-                                  d_trace_c, (cudaStream_t)stream));
+                                  d_trace_c, nullptr, nullptr, (cudaStream_t)stream));
+}
+
+int mlmc_path_trace_half_async(int level, uint64_t N, int integrator, const mlmc_params* p,
+                               uint64_t seed, uint64_t path_offset, void* d_half_f,
+                               void* d_half_c, void* stream) {
+  if (integrator != MLMC_BAOAB) return MLMC_EINVAL;
+  if (N && !d_half_f) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, seed, &hm);
+  if (rc) return rc;
+  if (hm.adapt) return MLMC_EINVAL;
+  LevelSpec ls;
+  if ((rc = level_spec(hm, level, &ls))) return rc;
+  if ((rc = check_stable(integrator, p, hm, ls))) return rc;
+  return cuda_status(launch_trace(p->precision, integrator, hm, ls, N, path_offset, nullptr,
+                                  nullptr, d_half_f, d_half_c, (cudaStream_t)stream));
 }
 
 }  // extern "C"
@@ -1164,67 +1228,70 @@ namespace mlmc {
 constexpr int kNoAllocItems = 4096;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[256 + kNoAllocItems * sizeof(Partial)];
 
-// Device address of the array, looked up once per device with that device
-// current.  Host code cannot use the symbol itself: on the host it names a
-// stand-in, not device memory.
-static void* g_noalloc_ptr[64];
+// Device address of the array, looked up once per CUDA context with that
+// context current.  Host code cannot use the symbol itself: on the host it
+// names a stand-in, not device memory.  The address belongs to a context
+// (the device's primary context, or one the caller made current), so the
+// cache is keyed on the context's unique id, which the driver never reuses:
+// after cudaDeviceReset, or in another context on the same device, the
+// lookup runs again.  The driver calls come through the runtime's entry
+// point query, so the library does not link the driver library.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+struct NoallocAddr {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+static NoallocAddr g_noalloc_addr[64];
+static int g_noalloc_n = 0;
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
 
-static int noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MLMC_ENODEV;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MLMC_ECUDA;
-    g_noalloc_ptr[dev] = p;
+// Id of the current context; 0 when none is current yet.  Caller holds g_mu.
+static int current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&g_ctx_get_current, 12000,
+                                         cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&g_ctx_get_id, 12000,
+                                         cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess ||
+        !g_ctx_get_current || !g_ctx_get_id) {
+      g_ctx_get_current = nullptr;
+      g_ctx_get_id = nullptr;
+      return MLMC_ENODEV;
+    }
   }
-  *out = g_noalloc_ptr[dev];
+  void* ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != 0) return MLMC_ECUDA;
+  *id = 0;
+  if (ctx && g_ctx_get_id(ctx, id) != 0) return MLMC_ECUDA;
   return MLMC_OK;
 }
 
-// Same split as the workspace form (finest level first, about 16 items per
-// resident block), enlarging the items until the plan fits kNoAllocItems.
-static int plan_noalloc(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
-                        const mlmc_params* p, int grid, ReqPlan* plan, uint32_t* n_items_out) {
-  double total = 0.0;
-  for (int r = 0; r < n_req; ++r) {
-    LevelSpec ls;
-    int rc = level_spec(hm, reqs[r].level, &ls);
-    if (rc) return rc;
-    if ((rc = check_stable(integ, p, hm, ls))) return rc;
-    total += (double)reqs[r].count * (double)steps_per_pair(ls);
-  }
-  double target = total / (16.0 * (double)grid);
-  if (target < 1.0) target = 1.0;
-  // the adaptive kernels run one pair per thread at a time
-  const uint64_t min_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
-  for (int pass = 0; pass < 64; ++pass) {
-    uint64_t items = 0;
-    bool too_big = false;
-    for (int k = 0; k < n_req; ++k) {
-      LevelSpec ls;
-      level_spec(hm, reqs[k].level, &ls);
-      const double ppi = std::floor(target / (double)steps_per_pair(ls));
-      uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
-      if (item_paths > 0x7FFFFFFFull) { item_paths = 0x7FFFFFFFull; too_big = true; }
-      const uint64_t n_it = reqs[k].count ? (reqs[k].count + item_paths - 1) / item_paths : 0;
-      plan[k].lv = ls;
-      plan[k].first = reqs[k].first;
-      plan[k].count = reqs[k].count;
-      plan[k].item_paths = (uint32_t)item_paths;
-      plan[k].n_items = (uint32_t)n_it;
-      plan[k].item_base = (uint32_t)items;
-      plan[k].path_steps = fixed_steps(hm, ls, reqs[k].count);
-      items += n_it;
-    }
-    if (items <= (uint64_t)kNoAllocItems) {
-      *n_items_out = (uint32_t)items;
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MLMC_ENODEV;
+  std::lock_guard<std::mutex> lk(g_mu);
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc) return rc;
+  for (int k = 0; id && k < g_noalloc_n; ++k)
+    if (g_noalloc_addr[k].ctx_id == id) {
+      *out = g_noalloc_addr[k].ptr;
       return MLMC_OK;
     }
-    if (too_big) break;
-    target *= 2.0;
+  // set-up: with no context current yet this lookup also creates the
+  // device's primary context and makes it current
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MLMC_ECUDA;
+  if ((rc = current_context_id(&id))) return rc;
+  if (id) {
+    if (g_noalloc_n == 64) g_noalloc_n = 0;   // a process with more contexts recycles the table
+    g_noalloc_addr[g_noalloc_n++] = NoallocAddr{id, p};
   }
-  return MLMC_EWORKSPACE;  // more than kNoAllocItems items of 2^31 - 1 pairs
+  *out = p;
+  return MLMC_OK;
 }
 
 }  // namespace mlmc
@@ -1244,9 +1311,15 @@ extern "C" int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int 
   const int prec = p->precision;
   const int grid = grid_for(prec, integrator, true, 0);
   if (grid <= 0) return MLMC_ENODEV;
+  // the workspace form's split (the requests are already finest level first,
+  // so the plan's order is theirs); only a batch of more than kNoAllocItems
+  // items gets larger items
   ReqPlan plan[kMaxReq];
+  int order[kMaxReq];
   uint32_t n_items = 0;
-  if ((rc = plan_noalloc(hm, reqs, n_req, integrator, p, grid, plan, &n_items))) return rc;
+  if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, (uint32_t)kNoAllocItems,
+                          MLMC_EWORKSPACE, plan, order, &n_items)))
+    return rc;
   unsigned int* counter = (unsigned int*)scratch;
   Partial* partials = (Partial*)((char*)scratch + 256);
   cudaStream_t st = (cudaStream_t)stream;

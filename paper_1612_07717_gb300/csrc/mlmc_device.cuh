@@ -354,9 +354,11 @@ __device__ __forceinline__ R baoab_post(const Model<R>& m, R hl2, R h2, Path<R>&
 
 // Fine sub-step with normal xi; returns the parity at the noise time (Sn)
 // and the O-step factor e (GL/BAOAB) used by the coarse coupling.
-template <int INTEG, typename R, bool EX>
+// tr.half_fine(n, p) sees BAOAB's state after the first half of fine step n.
+template <int INTEG, typename R, bool EX, class TR>
 __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
-                                          bool& flag, R xi, R& Sn, R& e) {
+                                          bool& flag, R xi, R& Sn, R& e, const TR& tr,
+                                          int64_t n) {
   if (INTEG == kSE) {
     Sn = p.S;
     e = R(0);
@@ -366,6 +368,7 @@ __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv,
     e = gl_step<R, EX>(m, lv.h, lv.hl2, p, flag, xi);
   } else {
     baoab_pre<R, EX>(m, lv.h2, p, flag);
+    tr.half_fine(n, p);
     Sn = p.S;
     e = baoab_post<R, EX>(m, lv.hl2, lv.h2, p, flag, xi);
   }
@@ -376,9 +379,10 @@ __device__ __forceinline__ void fine_step(const Model<R>& m, const Level<R>& lv,
 //   SE:       xi_c = S_c (S_a xa + S_b xb) / sqrt(2)          Eq. (euler_coupled_treatment)
 //   GL/BAOAB: xi_c = S_c (ea S_a xa + S_b xb) / sqrt(ea^2 + 1) Eq. (splitting_coupled_treatment)
 // With coupling = 1 (naive) all parities are taken as 1.
-template <int INTEG, typename R, bool EX>
+template <int INTEG, typename R, bool EX, class TR>
 __device__ __forceinline__ void coarse_step(const Model<R>& m, const Level<R>& lv, Path<R>& p,
-                                            bool& flag, R xa, R xb, R Sa, R Sb, R ea) {
+                                            bool& flag, R xa, R xb, R Sa, R Sb, R ea,
+                                            const TR& tr, int64_t k) {
   if (m.coupling) { Sa = R(1); Sb = R(1); }
   if (INTEG == kSE) {
     const R Sc = m.coupling ? R(1) : p.S;
@@ -390,6 +394,7 @@ __device__ __forceinline__ void coarse_step(const Model<R>& m, const Level<R>& l
     gl_step<R, EX>(m, lv.hc, lv.hcl2, p, flag, xc);
   } else {
     baoab_pre<R, EX>(m, lv.hc2, p, flag);
+    tr.half_coarse(k, p);
     const R Sc = m.coupling ? R(1) : p.S;
     const R xc = (Sc * rsqrt_(fma(ea, ea, R(1)))) * fma(ea * Sa, xa, Sb * xb);
     baoab_post<R, EX>(m, lv.hcl2, lv.hc2, p, flag, xc);
@@ -421,17 +426,25 @@ template <typename R>
 struct NoTrace {
   __device__ __forceinline__ void fine(int64_t, const Path<R>&) const {}
   __device__ __forceinline__ void coarse(int64_t, const Path<R>&) const {}
+  __device__ __forceinline__ void half_fine(int64_t, const Path<R>&) const {}
+  __device__ __forceinline__ void half_coarse(int64_t, const Path<R>&) const {}
 };
+// Rows of (z, w, S): f / c after every step, fh / ch (BAOAB) after the
+// first half of every step (the fold after its first A half-step); any of
+// them may be null.
 template <typename R>
 struct Trace {
-  R* f;  // (M+1) x 3
-  R* c;  // (M/2+1) x 3 or null
-  __device__ __forceinline__ void fine(int64_t row, const Path<R>& p) const {
-    f[3 * row] = p.z; f[3 * row + 1] = p.w; f[3 * row + 2] = p.S;
+  R* f;   // (M+1) x 3
+  R* c;   // (M/2+1) x 3
+  R* fh;  // M x 3
+  R* ch;  // M/2 x 3
+  __device__ __forceinline__ static void put(R* t, int64_t row, const Path<R>& p) {
+    if (t) { t[3 * row] = p.z; t[3 * row + 1] = p.w; t[3 * row + 2] = p.S; }
   }
-  __device__ __forceinline__ void coarse(int64_t row, const Path<R>& p) const {
-    if (c) { c[3 * row] = p.z; c[3 * row + 1] = p.w; c[3 * row + 2] = p.S; }
-  }
+  __device__ __forceinline__ void fine(int64_t row, const Path<R>& p) const { put(f, row, p); }
+  __device__ __forceinline__ void coarse(int64_t row, const Path<R>& p) const { put(c, row, p); }
+  __device__ __forceinline__ void half_fine(int64_t row, const Path<R>& p) const { put(fh, row, p); }
+  __device__ __forceinline__ void half_coarse(int64_t row, const Path<R>& p) const { put(ch, row, p); }
 };
 
 // ---------------------------------------------------------------------------
@@ -467,26 +480,26 @@ __device__ __forceinline__ void run_pair_impl(const Model<R>& m, const Level<R>&
     box_muller(x.z, x.w, xi2, xi3);
     const int64_t n4 = 4 * (int64_t)b;
     if (COUPLED) {
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea, tr, n4);
       tr.fine(n4 + 1, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sb, eb);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sb, eb, tr, n4 + 1);
       tr.fine(n4 + 2, f);
-      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi0, xi1, Sa, Sb, ea);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi0, xi1, Sa, Sb, ea, tr, n4 / 2);
       tr.coarse(n4 / 2 + 1, c);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea, tr, n4 + 2);
       tr.fine(n4 + 3, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sb, eb);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sb, eb, tr, n4 + 3);
       tr.fine(n4 + 4, f);
-      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi2, xi3, Sa, Sb, ea);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi2, xi3, Sa, Sb, ea, tr, n4 / 2 + 1);
       tr.coarse(n4 / 2 + 2, c);
     } else {
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi0, Sa, ea, tr, n4);
       tr.fine(n4 + 1, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi1, Sa, ea, tr, n4 + 1);
       tr.fine(n4 + 2, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi2, Sa, ea, tr, n4 + 2);
       tr.fine(n4 + 3, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi3, Sa, ea, tr, n4 + 3);
       tr.fine(n4 + 4, f);
     }
   }
@@ -499,15 +512,15 @@ __device__ __forceinline__ void run_pair_impl(const Model<R>& m, const Level<R>&
     const int64_t n0 = 4 * (int64_t)nblk;
     if (COUPLED) {
       // M even: tail is 2, one coarse step
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[0], Sa, ea);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[0], Sa, ea, tr, n0);
       tr.fine(n0 + 1, f);
-      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[1], Sb, eb);
+      fine_step<INTEG, R, EX>(m, lv, f, flag, xi[1], Sb, eb, tr, n0 + 1);
       tr.fine(n0 + 2, f);
-      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi[0], xi[1], Sa, Sb, ea);
+      coarse_step<INTEG, R, EX>(m, lv, c, flag, xi[0], xi[1], Sa, Sb, ea, tr, n0 / 2);
       tr.coarse(n0 / 2 + 1, c);
     } else {
       for (int j = 0; j < tail; ++j) {
-        fine_step<INTEG, R, EX>(m, lv, f, flag, xi[j], Sa, ea);
+        fine_step<INTEG, R, EX>(m, lv, f, flag, xi[j], Sa, ea, tr, n0 + j);
         tr.fine(n0 + j + 1, f);
       }
     }

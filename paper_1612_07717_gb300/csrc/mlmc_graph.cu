@@ -25,13 +25,13 @@ struct NvtxRange {
 namespace mlmc {
 
 constexpr int kLevels = MLMC_MAX_LEVELS;
-constexpr int kMaxIterations = 4 * kLevels;  // a driver pass count that cannot be exceeded
+constexpr int kMaxIterations = 4 * kLevels;  // default pass limit: more than a converging run takes
 
 // Driver state in the workspace's graph region.
 struct GState {
   int32_t L, pass, iter, converged, status, lmin, Lmax, n_init;
   int32_t M0, grid, done, items_per_block;
-  int32_t min_item, pad_;
+  int32_t min_item, max_iter;
   double eps, T;
   uint64_t Ndone[kLevels], dN[kLevels];
   uint64_t n[kLevels], bad[kLevels], steps[kLevels];
@@ -119,7 +119,8 @@ __device__ void write_result(const GState* g, mlmc_result* out) {
 }
 
 __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, int Lmax, int n_init,
-                             int M0, int grid, int ipb, int min_item, double eps, double T) {
+                             int M0, int grid, int ipb, int min_item, int max_iter, double eps,
+                             double T) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   GState* g = &r->g;
   memset(g, 0, sizeof(*g));
@@ -130,6 +131,7 @@ __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, in
   g->grid = grid;
   g->items_per_block = ipb;
   g->min_item = min_item;
+  g->max_iter = max_iter;
   g->eps = eps;
   g->T = T;
   g->L = lmin;
@@ -190,7 +192,7 @@ __global__ void k_graph_update(GraphRegion* r, const mlmc_level_result* __restri
       more = true;
     }
   }
-  if (more && g->iter >= kMaxIterations) {
+  if (more && g->iter >= g->max_iter) {       // the loop's watchdog
     g->status = MLMC_ETIMEOUT;
     more = false;
   }
@@ -229,10 +231,12 @@ static void graph_free(mlmc_graph_s* g) {
 
 extern "C" {
 
-int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
-                      void* workspace, size_t ws_bytes, mlmc_graph* out) {
+int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                         int max_passes, void* workspace, size_t ws_bytes, mlmc_graph* out) {
   if (!out || !p || !(eps > 0.0)) return MLMC_EINVAL;
   *out = nullptr;
+  if (max_passes < 0 || max_passes > kMaxIterations) return MLMC_EINVAL;
+  if (max_passes == 0) max_passes = kMaxIterations;
   if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
   if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2)
     return MLMC_EINVAL;
@@ -276,7 +280,8 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
                                    cudaStreamCaptureModeThreadLocal));
   k_graph_init<<<1, 32, 0, g->cap>>>(g->region, w.counter, p->level_min, p->L_max, p->n_init,
                                      p->M0, grid, items_per_block(prec, integrator),
-                                     (int)min_item_paths(prec, integrator), eps, p->T);
+                                     (int)min_item_paths(prec, integrator), max_passes, eps,
+                                     p->T);
   CK(cudaGetLastError());
   CK(cudaStreamEndCapture(g->cap, &g->graph));
   CK(cudaGraphGetNodes(g->graph, &init_node, &n_nodes));
@@ -301,6 +306,11 @@ int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t
 #undef CK
   *out = g;
   return MLMC_OK;
+}
+
+int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                      void* workspace, size_t ws_bytes, mlmc_graph* out) {
+  return mlmc_graph_create_ex(eps, integrator, p, seed, 0, workspace, ws_bytes, out);
 }
 
 int mlmc_graph_launch(mlmc_graph g, void* stream) {

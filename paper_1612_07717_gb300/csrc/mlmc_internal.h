@@ -114,7 +114,8 @@ cudaError_t launch_paths(int prec, int integ, const HostModel& hm, const LevelSp
                          uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
                          cudaStream_t st);
 cudaError_t launch_trace(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
-                         uint64_t N, uint64_t offset, void* d_tf, void* d_tc, cudaStream_t st);
+                         uint64_t N, uint64_t offset, void* d_tf, void* d_tc, void* d_thf,
+                         void* d_thc, cudaStream_t st);
 // Resident blocks per SM of the sums / multi-level kernels (occupancy query
 // and tuning table), and the planner's work items per resident block.
 int blocks_per_sm(int prec, int integ, bool multilevel);

@@ -220,10 +220,11 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
 #if MLMC_X2
 // Lane of a packed pair: the exact replay where the fast pass flagged a
 // multi-layer step, then the finiteness check, exactly as run_pair does.
+// Returns the diverged mark; the final states are updated in place.
 template <int INTEG, bool COUPLED>
-__device__ __forceinline__ void finish_lane(const Model<float>& m, const Level<float>& lv,
-                                            uint64_t i, float fz, float fw, float cz, float cw,
-                                            bool multi, Acc& acc) {
+__device__ __forceinline__ bool lane_final(const Model<float>& m, const Level<float>& lv,
+                                           uint64_t i, float& fz, float& fw, float& cz,
+                                           float& cw, bool multi) {
   bool bad = false;
   if (multi) {
     Path<float> f, c;
@@ -232,6 +233,14 @@ __device__ __forceinline__ void finish_lane(const Model<float>& m, const Level<f
   }
   bad |= !(isfinite(fz) && isfinite(fw));
   if (COUPLED) bad |= !(isfinite(cz) && isfinite(cw));
+  return bad;
+}
+
+template <int INTEG, bool COUPLED>
+__device__ __forceinline__ void finish_lane(const Model<float>& m, const Level<float>& lv,
+                                            uint64_t i, float fz, float fw, float cz, float cw,
+                                            bool multi, Acc& acc) {
+  const bool bad = lane_final<INTEG, COUPLED>(m, lv, i, fz, fw, cz, cw, multi);
   acc_add<float, COUPLED>(acc, m, fz, cz, bad);
 }
 
@@ -547,6 +556,8 @@ struct PathsArgs {
   int32_t* flags;   // N
   R* tf;            // trace: N x (M+1) x 3
   R* tc;            // trace: N x (M/2+1) x 3
+  R* thf;           // half-step trace (BAOAB): N x M x 3
+  R* thc;           // half-step trace (BAOAB): N x M/2 x 3
 };
 
 template <int INTEG, typename R, bool COUPLED>
@@ -563,14 +574,61 @@ __global__ void __launch_bounds__(kBlock) k_paths(const __grid_constant__ PathsA
   a.flags[j] = bad ? 1 : 0;
 }
 
+// Final states per pair through the path code of this translation unit's
+// tuning variant (its register budget; two pairs per thread on the packed
+// instructions in the MLMC_X2 units, thread g taking pairs 2g and 2g + 1 as
+// the level-sums kernel does), so the pairs the production kernels reduce
+// can be compared one by one.
+template <int INTEG, typename R, bool COUPLED>
+__global__ void __launch_bounds__(kBlock, MLMC_MINB) k_paths_v(const __grid_constant__ PathsArgs<R> a) {
+  if constexpr (MLMC_X2 && std::is_same<R, float>::value) {
+#if MLMC_X2
+    const uint64_t j = 2 * ((uint64_t)blockIdx.x * kBlock + threadIdx.x);
+    if (j >= a.N) return;
+    const StartX2 s0 = start_x2(a.m);
+    PathX2 f, c;
+    bool mx, my;
+    run_pair_x2_fast<INTEG, COUPLED>(a.m, a.lv, s0, a.offset + j, f, c, mx, my);
+    float fz = f.z.x, fw = f.w.x, cz = c.z.x, cw = c.w.x;
+    bool bad = lane_final<INTEG, COUPLED>(a.m, a.lv, a.offset + j, fz, fw, cz, cw, mx);
+    R* o = a.states + 4 * j;
+    o[0] = fz; o[1] = fw;
+    o[2] = COUPLED ? cz : 0.0f;
+    o[3] = COUPLED ? cw : 0.0f;
+    a.flags[j] = bad ? 1 : 0;
+    if (j + 1 < a.N) {                        // the last lane of an odd count is discarded
+      fz = f.z.y; fw = f.w.y; cz = c.z.y; cw = c.w.y;
+      bad = lane_final<INTEG, COUPLED>(a.m, a.lv, a.offset + j + 1, fz, fw, cz, cw, my);
+      o[4] = fz; o[5] = fw;
+      o[6] = COUPLED ? cz : 0.0f;
+      o[7] = COUPLED ? cw : 0.0f;
+      a.flags[j + 1] = bad ? 1 : 0;
+    }
+#endif
+  } else {
+    const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (j >= a.N) return;
+    Path<R> f, c;
+    bool bad;
+    run_pair<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, NoTrace<R>());
+    R* o = a.states + 4 * j;
+    o[0] = f.z; o[1] = f.w;
+    o[2] = COUPLED ? c.z : R(0);
+    o[3] = COUPLED ? c.w : R(0);
+    a.flags[j] = bad ? 1 : 0;
+  }
+}
+
 template <int INTEG, typename R, bool COUPLED>
 __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ PathsArgs<R> a) {
   const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (j >= a.N) return;
   const int64_t M = a.lv.M;
   Trace<R> tr;
-  tr.f = a.tf + (uint64_t)3 * (M + 1) * j;
+  tr.f = a.tf ? a.tf + (uint64_t)3 * (M + 1) * j : nullptr;
   tr.c = (COUPLED && a.tc) ? a.tc + (uint64_t)3 * (M / 2 + 1) * j : nullptr;
+  tr.fh = a.thf ? a.thf + (uint64_t)3 * M * j : nullptr;
+  tr.ch = (COUPLED && a.thc) ? a.thc + (uint64_t)3 * (M / 2) * j : nullptr;
   Path<R> f, c;
   bool bad;
   run_pair_exact<INTEG, R, COUPLED>(a.m, a.lv, a.offset + j, f, c, bad, tr);
@@ -601,6 +659,12 @@ template <int I, typename R, bool C>
 struct PathsK {
   static void launch(dim3 g, const PathsArgs<R>& a, cudaStream_t st) {
     k_paths<I, R, C><<<g, kBlock, 0, st>>>(a);
+  }
+};
+template <int I, typename R, bool C>
+struct PathsVK {
+  static void launch(dim3 g, const PathsArgs<R>& a, cudaStream_t st) {
+    k_paths_v<I, R, C><<<g, kBlock, 0, st>>>(a);
   }
 };
 template <int I, typename R, bool C>
@@ -696,8 +760,10 @@ cudaError_t pdf_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64
 template <typename R>
 cudaError_t paths_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
                        uint64_t offset, void* states, int32_t* flags, void* tf, void* tc,
-                       bool trace, cudaStream_t st) {
+                       void* thf, void* thc, bool trace, cudaStream_t st) {
   PathsArgs<R> a;
+  a.thf = (R*)thf;
+  a.thc = (R*)thc;
   a.m = make_model<R>(hm);
   a.lv = make_level<R>(ls);
   a.N = N;
@@ -710,6 +776,26 @@ cudaError_t paths_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint
   if (N == 0) return cudaSuccess;
   if (trace) return launch3<R, TraceK>(integ, ls.coupled, g, a, st);
   return launch3<R, PathsK>(integ, ls.coupled, g, a, st);
+}
+
+template <typename R>
+cudaError_t paths_variant_impl(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t N,
+                               uint64_t offset, void* states, int32_t* flags, cudaStream_t st) {
+  PathsArgs<R> a;
+  a.m = make_model<R>(hm);
+  a.lv = make_level<R>(ls);
+  a.N = N;
+  a.offset = offset;
+  a.states = (R*)states;
+  a.flags = flags;
+  a.tf = nullptr;
+  a.tc = nullptr;
+  a.thf = nullptr;
+  a.thc = nullptr;
+  if (N == 0) return cudaSuccess;
+  const uint64_t per_block = (MLMC_X2 && std::is_same<R, float>::value) ? 2 * kBlock : kBlock;
+  const dim3 g((unsigned)((N + per_block - 1) / per_block));
+  return launch3<R, PathsVK>(integ, ls.coupled, g, a, st);
 }
 
 template <typename R>

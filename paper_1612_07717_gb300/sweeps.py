@@ -14,9 +14,6 @@ Both use FP32 paths with FP64 sums, so the step counts compare the two
 algorithms on equal terms.
 
 Run on a GPU: ``python -m paper_1612_07717_gb300.sweeps [out.json]``.
-``python -m paper_1612_07717_gb300.sweeps level se|gl|baoab LEVEL LOG2N X_ADAPT`` times
-one level-sums launch of the paper scenario (X_ADAPT 0: uniform timesteps),
-the unit a profiler capture of the level kernels is taken on.
 ``python -m paper_1612_07717_gb300.sweeps time_to_eps`` times MLMC against
 plain FP64 Monte Carlo in the 600 m layer for eps = H 2^-9 .. H 2^-13;
 ``python -m paper_1612_07717_gb300.sweeps scenarios`` runs the integrator and
@@ -207,34 +204,10 @@ def pdf_release_table(eps_density=4e-3, k=20, releases=(0.05, 0.1, 0.2), seed=5)
     return out
 
 
-def time_level(integ, level, n, z_adapt=0.0, reps=3, seed=4):
-    """Time level_sums of n pairs on one level (the last of reps launches)."""
-    import torch
-    p = make_params(dict(W.PAPER, z_adapt=z_adapt), precision=FP32)
-    ws = Workspace(p)
-    from . import level_sums
-    for _ in range(reps - 1):
-        level_sums(level, n, integ, p, seed, workspace=ws)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    s = level_sums(level, n, integ, p, seed, workspace=ws)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    return dict(level=level, pairs=n, z_adapt=z_adapt, path_steps=s["path_steps"], ms=ms,
-                path_steps_per_s=s["path_steps"] / (ms * 1e-3))
-
-
 if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "scenarios":
     print(json.dumps(scenario_precision_sweep(), indent=1))
 elif __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "time_to_eps":
     print(json.dumps(bl600_time_to_eps(), indent=1))
-elif __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "level":
-    integ = {"se": SE, "gl": GL, "baoab": BAOAB}[sys.argv[2]]
-    print(json.dumps(time_level(integ, int(sys.argv[3]), 1 << int(sys.argv[4]),
-                                float(sys.argv[5]))))
 elif __name__ == "__main__":
     res = dict(scenario="paper (H = 1, u* = 0.2, T = 1, X0 = 0.05, U0 = 0.1, eps_reg = 0.01, M0 = 40)",
                cost=paper_cost_sweep(), adaptive=adaptive_cost_sweep(),

@@ -4,10 +4,13 @@ per path with the reflection near-tie rule.
 
 Tolerances (per path, final position):
   FP32 paths: |z_gpu - z_oracle| <= 1e-4 H.  A path may be exempt only when
-    the two disagree on a reflection decision: at the first time point where
-    the parities differ the oracle's path is within 1e-5 H of a wall (plus
-    |w| h for BAOAB, whose folds happen at half-steps that the trace does not
-    record).  At most 1e-3 of the paths (and at least 2) may be exempt.
+    the two disagree on a reflection decision: at the first row where the
+    parities differ the oracle's path is within 1e-5 H of a wall.  For BAOAB
+    the rows include the state after the first half of every step (GPU and
+    oracle half-step traces), so every fold has its row: a fold taken half a
+    step apart on the two sides, which the full-step rows alone hide, is
+    located exactly.  At most 1e-3 of the paths (and at least 2) may be
+    exempt.
   FP64 paths: |dz| <= 1e-9 H, same exemption rule.
 """
 import numpy as np
@@ -30,8 +33,21 @@ def tolerance(precision, H):
     return (1e-4 if precision == G.FP32 else 1e-9) * H
 
 
+def _interleave(full, half):
+    """Full-step rows and BAOAB's half-step rows in time order: full 0, half 0,
+    full 1, half 1, ..., full M (row r at time r / 2 steps)."""
+    out = np.empty((full.shape[0] + half.shape[0], full.shape[1]))
+    out[0::2] = full
+    out[1::2] = half
+    return out
+
+
 def near_tie(d, integ, level, i, seed, precision, tol):
-    """True when path pair i differs only through a reflection near-tie."""
+    """True when path pair i differs only through a reflection near-tie: the
+    two first disagree on a parity at a fold that left the oracle's path
+    within 1e-5 H of a wall, and their positions had not separated before.
+    For BAOAB the rows after each first half-step are included on both sides,
+    so every fold of the path has a row."""
     pg = gpu_params(d, precision)
     po = oracle_params(d, precision)
     H = po.H
@@ -40,19 +56,26 @@ def near_tie(d, integ, level, i, seed, precision, tol):
     tc = tc[0].double().cpu().numpy()
     r = O.path(po, integ, level, i, seed, trace=True)
     of, oc = r["trace_f"], r["trace_c"]
-    M = po.M0 << level
-    h = po.T / M
     coupled = level > po.level_min
-    # (gpu trace, oracle trace, step, fine-index units per row)
-    pairs = [(tf, of, h, 1)]
+    unit_f, unit_c = 1.0, 2.0            # fine steps per row
+    if integ == O.BAOAB:
+        hf, hc = G.path_trace_half(level, 1, integ, pg, seed, path_offset=i)
+        rh = O.path_half(po, integ, level, i, seed)
+        tf = _interleave(tf, hf[0].double().cpu().numpy())
+        of = _interleave(of, rh["half_f"])
+        tc = _interleave(tc, hc[0].double().cpu().numpy())
+        oc = _interleave(oc, rh["half_c"])
+        unit_f, unit_c = 0.5, 1.0
+    # (gpu rows, oracle rows, fine steps per row)
+    pairs = [(tf, of, unit_f)]
     if coupled:
-        pairs.append((tc, oc, 2 * h, 2))
+        pairs.append((tc, oc, unit_c))
     flips, devs = [], []
-    for g, o, hh, unit in pairs:
+    for g, o, unit in pairs:
         ds = g[:, 2] != o[:, 2]
         if ds.any():
-            k = int(np.argmax(ds))
-            flips.append((k * unit, o[k, 0], abs(o[k, 1]), hh))
+            k = int(np.argmax(ds))          # the fold of row k is where the parities part
+            flips.append((k * unit, o[k, 0]))
         dz = np.abs(g[:, 0] - o[:, 0]) > tol
         if dz.any():
             devs.append(int(np.argmax(dz)) * unit)
@@ -60,20 +83,23 @@ def near_tie(d, integ, level, i, seed, precision, tol):
         return False
     if not flips:
         return False            # positions separated with no reflection disagreement
-    t_flip, z, w, hh = min(flips)
+    t_flip, z = min(flips)
     if min(devs) < t_flip:
         return False            # separated before the first parity flip
-    win = 1e-5 * H + (w * hh if integ == O.BAOAB else 0.0)
+    win = 1e-5 * H
     return bool(z < win or H - z < win)
 
 
-def compare_paths(d, integ, level, N, offset=0, seed=1, precision=G.FP32, max_exempt=None):
-    """Run N pairs on both sides; return (max |dz| over non-exempt, n_exempt, gpu states)."""
+def compare_paths(d, integ, level, N, offset=0, seed=1, precision=G.FP32, max_exempt=None,
+                  variant=None):
+    """Run N pairs on both sides (the GPU side through tuning variant
+    `variant`'s path code when given); return (max |dz| over non-exempt,
+    n_exempt, gpu states, gpu flags, oracle states)."""
     pg = gpu_params(d, precision)
     po = oracle_params(d, precision)
     H = po.H
     tol = tolerance(precision, H)
-    states, flags = G.level_paths(level, N, integ, pg, seed, path_offset=offset)
+    states, flags = G.level_paths(level, N, integ, pg, seed, path_offset=offset, variant=variant)
     gs = states.double().cpu().numpy()
     gf = flags.cpu().numpy()
     os_, of = O.paths(po, integ, level, N, offset, seed)

@@ -41,3 +41,25 @@ def test_graph_relaunch_is_bitwise_reproducible():
     for k in ("estimate", "est_variance", "N", "V", "mean_y", "L", "total_path_steps"):
         assert a[k] == b[k], k
     assert a["converged"] == 1
+
+
+def test_watchdog_ends_the_device_loop_and_leaves_the_device_usable():
+    # A tolerance that needs several passes, with the loop's pass limit set to
+    # 2: the update kernel ends the loop and the result reports MLMC_ETIMEOUT
+    # (no spin, no trap); the next graph on the same workspace runs normally.
+    p = G.make_params(W.bl600(G.BAOAB, L_max=10, n_init=2000))
+    eps = 600 * 2.0 ** -9
+    ws = G.Workspace(p)
+    ge = G.GraphEstimator(eps, G.BAOAB, p, 11, workspace=ws, max_passes=2)
+    ge.launch()
+    with pytest.raises(G.MLMCError) as e:
+        ge.result()
+    assert e.value.code == G.ETIMEOUT
+    ge.close()
+    with pytest.raises(G.MLMCError) as e:
+        G.GraphEstimator(eps, G.BAOAB, p, 11, workspace=ws, max_passes=4 * 32 + 1)
+    assert e.value.code == G.EINVAL
+    r = G.estimate_graph(eps, G.BAOAB, p, 11, workspace=ws)
+    assert r["status"] == G.OK and r["converged"] == 1
+    ref = G.estimate(eps, G.BAOAB, p, 11)
+    assert r["L"] == ref["L"]

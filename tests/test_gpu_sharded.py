@@ -8,7 +8,11 @@ other; only the hosts meet in the reduction.
   the same levels and sample counts, estimates equal to FP64 rounding;
 * a rank whose launch fails still joins the reduction, so every rank
   returns an error instead of waiting;
-* a reduce hook that fails gives MLMC_ECOMM.
+* a reduce hook that fails gives MLMC_ECOMM;
+* with FP64 paths the two gloo ranks' sample counts equal the FP64 oracle
+  driver's and their estimate equals its estimate to 1e-10: the all-reduce
+  of the per-level sums preserves the telescoping estimator (Eqs.
+  telescoping_sum and Yhatell) whatever the split.
 """
 import os
 import socket
@@ -19,6 +23,7 @@ import pytest
 import torch
 import torch.multiprocessing as mp
 
+from oracle import oracle as O
 from paper_1612_07717_gb300 import workloads as W
 
 import paper_1612_07717_gb300 as G
@@ -28,8 +33,8 @@ pytestmark = pytest.mark.gpu
 EPS = 2e-3 * 600
 
 
-def _params():
-    return G.make_params(W.bl600(G.GL, n_init=5000, L_max=8))
+def _params(precision=G.FP32):
+    return G.make_params(W.bl600(G.GL, n_init=5000, L_max=8), precision=precision)
 
 
 class HostSum:
@@ -124,13 +129,13 @@ def _free_port():
     return port
 
 
-def _proc(rank, world, port, out_path):
+def _proc(rank, world, port, out_path, precision=G.FP32):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     torch.cuda.set_device(0)
-    r = G.estimate_sharded(EPS, G.GL, _params(), 13, rank, world, G.torch_allreduce())
+    r = G.estimate_sharded(EPS, G.GL, _params(precision), 13, rank, world, G.torch_allreduce())
     np.save(out_path + "_%d.npy" % rank,
             np.array([r["L"]] + r["N"] + list(r["estimate"]) + [r["total_path_steps"]],
                      dtype=np.float64))
@@ -152,3 +157,21 @@ def test_two_process_ranks_over_gloo_give_the_single_process_result(tmp_path):
         assert np.array_equal(got[:n], want[:n])
         assert np.allclose(got[n:n + 2], want[n:n + 2], rtol=1e-12, atol=1e-12)
         assert got[-1] == want[-1]
+
+
+def test_two_process_fp64_ranks_over_gloo_equal_the_oracle_driver(tmp_path):
+    out = str(tmp_path / "res64")
+    mp.start_processes(_proc, args=(2, _free_port(), out, G.FP64), nprocs=2, join=True,
+                       start_method="spawn")
+    po = O.make_params(W.bl600(G.GL, n_init=5000, L_max=8), uniform_map=O.U32)
+    o = O.estimate(po, O.GL, EPS, seed=13)
+    assert o["converged"] == 1
+    for rank in range(2):
+        got = np.load(out + "_%d.npy" % rank)
+        L = int(got[0])
+        n = 1 + (L - po.level_min + 1)
+        assert L == o["L"]
+        assert [int(x) for x in got[1:n]] == o["N"]
+        assert got[n] == pytest.approx(o["estimate"][0], rel=1e-10)
+        assert got[n + 1] == pytest.approx(o["estimate"][1], rel=1e-10, abs=1e-12)
+        assert int(got[-1]) == o["total_path_steps"]
