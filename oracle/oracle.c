@@ -302,9 +302,11 @@ static double normal_at(const orc_params* p, int level, uint64_t i, uint64_t see
 /* regularised profile), and the last step of a path shortened to end at T. */
 /* lambda decreases with height, so the ratio is below 1 exactly when the   */
 /* clamped X_n lies below X_adapt; the step is then shortened to           */
-/* floor(1024 ratio) / 1024 of h (at least 1/1024, which the parameter     */
-/* check guarantees): the same rule on every level, never longer than the   */
-/* paper's step, and a decision that rounding of lambda rarely flips.       */
+/* floor(Q ratio) / Q of h, Q = 2^adapt_q (1024 by default; at least 1/1024 */
+/* of h, which the parameter check guarantees): the same rule on every      */
+/* level, never longer than the paper's step, and a decision that rounding  */
+/* of lambda rarely flips.  With adapt_q = 30 it is the paper's rule to     */
+/* 1e-9 relative.                                                           */
 /* Time is counted in ticks of h_0 / 2^40 with h_0 = T / M0, so that h_l =  */
 /* 2^(40 - l) ticks and every step is a whole number of ticks; the fine and */
 /* coarse time points of a pair are compared exactly.                       */
@@ -348,13 +350,15 @@ static void adapt_begin(const orc_params* p, astep_t* a, double lam_a, int64_t h
   int64_t n = hmax;
   double m = fabs(Xc - p->z_adapt) / H;      /* margin of the "below X_adapt" test */
   if (Xc < p->z_adapt) {
-    const double r = 1024.0 * (lam_a / a->c.lambda);
+    const int q = p->adapt_q > 0 ? p->adapt_q : 10;
+    const double Q = ldexp(1.0, q);
+    const double r = Q * (lam_a / a->c.lambda);
     double k = floor(r);
-    const double mk = (r - k < k + 1.0 - r ? r - k : k + 1.0 - r) / 1024.0;
+    const double mk = (r - k < k + 1.0 - r ? r - k : k + 1.0 - r) / Q;
     if (mk < m) m = mk;                        /* margin of the floor */
     if (k < 1.0) k = 1.0;
-    if (k > 1024.0) k = 1024.0;
-    n = (int64_t)k * (hmax / 1024);
+    if (k > Q) k = Q;
+    n = (int64_t)k * (hmax >> q);
   }
   if (t > 0 && m < *tie) *tie = m;             /* the release point is exact on any side */
   if (n > T_ticks - t) n = T_ticks - t;
@@ -393,7 +397,8 @@ static void adapt_step(const orc_params* p, int integ, astep_t* a, double h, dou
 
 static int path_adaptive(const orc_params* p, int integ, int level, uint64_t i, uint64_t seed,
                          orc_path_out* out) {
-  if (integ == ORC_BAOAB || level > ORC_TICK_BITS - 10) return -1;
+  const int q = p->adapt_q > 0 ? p->adapt_q : 10;
+  if (integ == ORC_BAOAB || q > 30 || level > ORC_TICK_BITS - q) return -1;
   const int coupled = level > p->level_min;
   const double lam_a = coefficients(p, p->z_adapt).lambda;
   const double h0 = p->T / (double)p->M0;

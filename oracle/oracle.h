@@ -52,7 +52,11 @@ typedef struct {
   double qoi_a, qoi_b;  /* interval of the smoothed QoI [m]                          */
   double smooth_delta;  /* smoothing width delta [m]                                 */
   int32_t smooth_r;     /* smoothing order r (p_r has degree r + 1)                  */
-  int32_t pad2_;
+  int32_t adapt_q;      /* adaptive timesteps: a shortened step is a whole number
+                           of 2^-adapt_q of h; 0 means 10 (the CUDA library's
+                           1/1024); up to 30, where the rule is the paper's
+                           min(h, lambda(X_adapt) / lambda(X_n) h) to 1e-9
+                           relative (needs level <= 40 - adapt_q)              */
   double z_adapt;       /* > 0: adaptive timesteps with reference height X_adapt [m]
                            (Section 7.2, SE and GL only; needs z_adapt <= H,
                            M0 <= 2^22 and lambda(X_adapt) >= lambda_max / 1024);
@@ -114,11 +118,11 @@ int orc_normalise(orc_params* p);
  * p->z_adapt > 0 the pair takes the adaptive, non-nested timesteps of
  * Section 7.2 on the merged time grid; time is counted in ticks of
  * h_0 / 2^40 (h_0 = T / M0) and each adaptive step is a whole number of
- * ticks; a shortened step is floor(1024 lambda(X_adapt) / lambda(X_n)) / 1024
- * of h.  out->tie is the smallest margin of a step decision after the
- * release: |X_n - X_adapt| / H for "below X_adapt", and the distance of
- * 1024 lambda(X_adapt) / lambda(X_n) to an integer, over 1024, for the
- * floor.  Where it is tiny, a rounding difference can change a step and with
+ * ticks; a shortened step is floor(Q lambda(X_adapt) / lambda(X_n)) / Q of h,
+ * Q = 2^adapt_q (1024 by default).  out->tie is the smallest margin of a
+ * step decision after the release: |X_n - X_adapt| / H for "below X_adapt",
+ * and the distance of Q lambda(X_adapt) / lambda(X_n) to an integer, over Q,
+ * for the floor.  Where it is tiny, a rounding difference can change a step and with
  * it the merged grid.  out->gap is the smallest |t_f - t_c| / h over distinct next
  * fine and coarse time points (a rounding difference there only moves a
  * short interval between neighbouring steps).  Returns 0, or -1 on bad

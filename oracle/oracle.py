@@ -26,7 +26,7 @@ class Params(C.Structure):
         ("L_max", C.c_int32), ("coupling", C.c_int32), ("drift_outside", C.c_int32),
         ("n_init", C.c_int32), ("uniform_map", C.c_int32), ("stream_id", C.c_uint32),
         ("qoi1_mode", C.c_int32), ("qoi_a", C.c_double), ("qoi_b", C.c_double),
-        ("smooth_delta", C.c_double), ("smooth_r", C.c_int32), ("pad2_", C.c_int32),
+        ("smooth_delta", C.c_double), ("smooth_r", C.c_int32), ("adapt_q", C.c_int32),
         ("z_adapt", C.c_double),
     ]
 
@@ -89,7 +89,7 @@ _DEFAULTS = dict(u_star=0.2, f_coriolis=1e-4, H=0.0, kappa_sigma=1.3, kappa_tau=
                  eps_reg_frac=1e-3, z0=0.0, w0=0.0, T=1.0, qoi_threshold=0.0, w0_mode=0, M0=8,
                  level_min=0, L_max=10, coupling=0, drift_outside=0, n_init=10000,
                  uniform_map=U32, stream_id=0, qoi1_mode=0, qoi_a=0.0, qoi_b=0.0,
-                 smooth_delta=0.0, smooth_r=4, z_adapt=0.0)
+                 smooth_delta=0.0, smooth_r=4, z_adapt=0.0, adapt_q=0)
 
 
 def make_params(d=None, **kw):

@@ -16,6 +16,11 @@ AdaptivityIncrementSplitting) and Section 7.3 of the paper.
   like h_l^2 with the reflection-aware increments (not with all S = 1),
   adaptivity lowers Var[Y_l] at a given h_l, the SE bias falls about 6x and
   the GL bias grows about 3x.
+* The step rule that the library uses, a shortened step rounded down to a
+  1024th of h, against the paper's min(h, lambda(X_adapt) / lambda(X_n) h)
+  (the oracle's adapt_q = 30: a 2^-30 of h, 1e-9 relative to the exact
+  rule): E[Y_l] and Var[Y_l] agree within 3 standard errors on levels 2..5
+  of the Section 7.3 scenario, for SE and GL.
 """
 import json
 import math
@@ -69,8 +74,9 @@ def adaptive_pair(p, integ, level, i, seed):
         H, e = p["H"], p["eps_reg_frac"] * p["H"]
         n = P["hmax"]
         if min(max(P["X"], e), H - e) < p["z_adapt"]:      # lambda(X_n) > lambda(X_adapt)
-            k = min(max(math.floor(1024 * (lam_a / c[1])), 1), 1024)
-            n = k * (P["hmax"] // 1024)
+            Q = 1 << (p.get("adapt_q") or 10)
+            k = min(max(math.floor(Q * (lam_a / c[1])), 1), Q)
+            n = k * (P["hmax"] // Q)
         n = min(n, T_ticks - t)
         P.update(c=c, n=n, end=t + n, ivals=[])
 
@@ -132,6 +138,8 @@ CASES = [
     (O.SE, dict(W.PAPER, z_adapt=0.05), 1),
     (O.GL, dict(W.PAPER, z_adapt=0.05, coupling=1), 1),
     (O.GL, dict(W.PAPER, z_adapt=0.05, z0=0.004, uniform_map=0), 0),
+    (O.SE, dict(W.PAPER, z_adapt=0.05, adapt_q=30), 2),     # the unquantized step rule
+    (O.GL, dict(W.PAPER, z_adapt=0.05, adapt_q=30), 3),
 ]
 
 
@@ -269,3 +277,34 @@ def test_adaptive_parameters_are_checked():
     p = O.make_params(dict(W.PAPER, z_adapt=0.05))
     with pytest.raises(ValueError):
         O.path(p, O.BAOAB, 1, 0, 1)                        # Section 7.2 covers SE and GL
+
+
+def _batched_stats(p, integ, level, n_batch, batches, seed):
+    """Mean and variance of Y_l over batches of consecutive pairs, with the
+    standard error of each from the spread of the batch estimates."""
+    ms, vs = [], []
+    for b in range(batches):
+        s = O.level_sums(p, integ, level, n_batch, b * n_batch, seed)
+        n = s["n"]
+        m = s["sum"][0][0] / n
+        ms.append(m)
+        vs.append((s["sum"][0][1] - n * m * m) / (n - 1))
+    ms, vs = np.array(ms), np.array(vs)
+    return (ms.mean(), ms.std(ddof=1) / math.sqrt(batches), vs.mean(),
+            vs.std(ddof=1) / math.sqrt(batches))
+
+
+@pytest.mark.parametrize("integ", [O.SE, O.GL])
+def test_quantized_step_rule_matches_the_exact_rule(integ):
+    # Section 7.2, Eq. (adaptive h), in the Section 7.3 scenario: the two
+    # rules draw the same normals per merged interval but their grids part
+    # after the first shortened step, so the comparison is statistical.
+    za = GOLDEN["adaptive_bias_ratio"]["X_adapt"]
+    quant = O.make_params(dict(W.PAPER, z_adapt=za))
+    exact = O.make_params(dict(W.PAPER, z_adapt=za, adapt_q=30))
+    for level in (2, 3, 4, 5):
+        n_batch = 8000 if level <= 3 else 3000
+        mq, smq, vq, svq = _batched_stats(quant, integ, level, n_batch, 8, 17)
+        me, sme, ve, sve = _batched_stats(exact, integ, level, n_batch, 8, 17)
+        assert abs(mq - me) <= 3 * math.hypot(smq, sme), (level, mq, me, smq, sme)
+        assert abs(vq - ve) <= 3 * math.hypot(svq, sve), (level, vq, ve, svq, sve)
