@@ -395,47 +395,69 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
  * the paper's introduction motivates).  Each query is an adaptive MLMC
  * estimate (the rule of mlmc_estimate) of its own scenario and tolerance;
  * its Philox stream is p->stream_id, the key is the server's seed.
- *   mlmc_server_workspace_bytes  device workspace for max_active queries
- *                                (model slots; the request table, results
- *                                and partials of each launch in flight)
+ *
+ * Device state.  An admitted query owns a record in a pool that the server
+ * carves from the caller's workspace: its Model and its whole per-level
+ * state -- for every level level_min..L_max the twelve FP64 sums, the pair,
+ * diverged and step counts, the samples folded and the pass targets -- and
+ * the driver's level, pass and plan.  After each launch a fold kernel adds
+ * every chunk's sums into its query's record and, once a pass is complete,
+ * applies Eq. 12's sample sizes and the bias test on the device; the host
+ * reads back only each touched query's plan (the samples of its next pass)
+ * or, when it is done, its result.
+ *
+ * Admission is by memory: a queued query is admitted, in arrival order,
+ * when a record of its size -- mlmc_server_query_bytes(p), which grows with
+ * its number of levels -- fits in the free part of the pool (first fit; the
+ * head of the queue is never overtaken) and fewer than max_active queries
+ * are active.  A query whose record exceeds the whole pool is refused at
+ * submit (MLMC_EWORKSPACE).
+ *
+ *   mlmc_server_workspace_bytes  device workspace: the launch buffers plus a
+ *                                pool of max_active records of 17 levels
+ *                                (0 gives the launch buffers alone; any
+ *                                larger workspace is all pool)
+ *   mlmc_server_query_bytes      bytes of one query's record
  *   mlmc_server_create   binds the workspace; work queued on `stream`
  *                        before the call is ordered before the server's
- *                        launches, which run on four streams of its own;
- *                        allocates those streams, their events and pinned
- *                        host staging buffers (no device memory)
+ *                        launches, which run on four streams of its own, the
+ *                        folds on a fifth; allocates those streams, their
+ *                        events and pinned host staging buffers (no device
+ *                        memory)
  *   mlmc_server_submit   validates and queues a query; returns its id
- *   mlmc_server_tick     folds the launches that have completed (oldest
- *                        first), admits queued queries while a slot is
- *                        free, and puts one more launch in flight (at most
- *                        four): one persistent launch (of the one-pair
- *                        kernel, variant 4, whatever the tuning table
- *                        holds: the finest work items) over chunks (at most
- *                        2^26 path-steps each) of the active queries'
- *                        pending passes -- least pending work first, a
- *                        waiting query's priority doubling every launch --
- *                        up to 2^28 path-steps, 2048 requests and 32768
- *                        work items, holding only pairs at most 4 times as
- *                        long as its first chunk's (or 2048 path-steps);
- *                        when all four are in flight, or nothing is left
- *                        to issue, it first waits for the oldest.  A folded
- *                        chunk enters its query in chunk order; a query
- *                        whose pass is folded advances its driver and may
- *                        finish.  n_done: queries finished in this call;
- *                        n_active: queries left (active and queued).  After
- *                        a CUDA error every later call returns that error
- *                        (launches in flight may be lost)
+ *   mlmc_server_tick     takes the plans of the launches whose folds have
+ *                        completed (oldest first), admits queued queries
+ *                        while their records fit, and puts one more launch
+ *                        in flight (at most four): one persistent launch
+ *                        (of the one-pair kernel, variant 4, whatever the
+ *                        tuning table holds: the finest work items) over
+ *                        chunks (at most 2^26 path-steps each) of the
+ *                        active queries' pending passes -- least pending
+ *                        work first, a waiting query's priority doubling
+ *                        every launch -- up to 2^28 path-steps, 2048
+ *                        requests and 32768 work items, holding only pairs
+ *                        at most 4 times as long as its first chunk's (or
+ *                        2048 path-steps), followed by its fold; when all
+ *                        four are in flight, or nothing is left to issue, it
+ *                        first waits for the oldest.  n_done: queries
+ *                        finished in this call; n_active: queries left
+ *                        (active and queued).  After a CUDA error every
+ *                        later call returns that error (launches in flight
+ *                        may be lost)
  *   mlmc_server_poll     1 while the query runs; its final status (MLMC_OK,
  *                        MLMC_ENOTCONV, MLMC_ENONFINITE) with the result and
  *                        its submit-to-finish latency once done
  *   mlmc_server_release  forgets a finished query
  *   mlmc_server_stats    out = {ticks, finished, path-steps, busy seconds,
  *                        active, queued}
+ *   mlmc_server_pool     out = {record bytes in use, pool bytes}
  * A pass's chunks, their split into work items and their folding order
  * depend only on the query (and the server's grid), so a query's result is
  * bitwise the same alone and in any mix; the scheduling decides only when a
  * chunk runs.  mlmc_server_destroy waits for the launches in flight. */
 typedef struct mlmc_server_s* mlmc_server;
 size_t mlmc_server_workspace_bytes(int max_active);
+size_t mlmc_server_query_bytes(const mlmc_params* p);
 int mlmc_server_create(int integrator, int precision, int max_active, uint64_t seed,
                        void* workspace, size_t ws_bytes, void* stream, mlmc_server* out);
 int mlmc_server_submit(mlmc_server s, const mlmc_params* p, double eps, uint64_t* query_id);
@@ -443,6 +465,7 @@ int mlmc_server_tick(mlmc_server s, int* n_done, int* n_active);
 int mlmc_server_poll(mlmc_server s, uint64_t query_id, mlmc_result* out, double* latency_s);
 int mlmc_server_release(mlmc_server s, uint64_t query_id);
 int mlmc_server_stats(mlmc_server s, double out[6]);
+int mlmc_server_pool(mlmc_server s, uint64_t out[2]);
 int mlmc_server_destroy(mlmc_server s);
 
 /* ---------------------------------------------------------- path outputs */

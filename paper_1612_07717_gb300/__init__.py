@@ -138,6 +138,9 @@ def lib():
         L.mlmc_get_tuning.argtypes = [i32, i32, C.POINTER(C.c_int32)]
         L.mlmc_server_workspace_bytes.restype = C.c_size_t
         L.mlmc_server_workspace_bytes.argtypes = [i32]
+        L.mlmc_server_query_bytes.restype = C.c_size_t
+        L.mlmc_server_query_bytes.argtypes = [C.POINTER(Params)]
+        L.mlmc_server_pool.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.mlmc_server_create.argtypes = [i32, i32, i32, u64, vp, C.c_size_t, vp, C.POINTER(vp)]
         L.mlmc_server_submit.argtypes = [vp, C.POINTER(Params), C.c_double, C.POINTER(u64)]
         L.mlmc_server_tick.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -604,20 +607,32 @@ def path_trace_half(level, N, integrator, params, seed, path_offset=0, stream=No
     return hf, hc
 
 
+def server_query_bytes(params):
+    """Bytes of the device record a query with these parameters takes in a
+    server's pool (``mlmc_server_query_bytes``)."""
+    return int(lib().mlmc_server_query_bytes(C.byref(params)))
+
+
 class Server:
     """Continuous-batching server of dispersion queries (``mlmc_server_*``).
 
     ``submit`` queues a query (a ``Params`` with its own scenario and
-    ``stream_id``) with its tolerance; ``tick`` folds the completed launches,
-    retires the finished queries and puts one more batched launch in flight
-    (up to four at once); ``poll`` returns a finished query's result and
-    latency.
+    ``stream_id``) with its tolerance; ``tick`` takes the folded launches,
+    retires the finished queries, admits queued ones whose device records
+    fit, and puts one more batched launch in flight (up to four at once);
+    ``poll`` returns a finished query's result and latency.  The workspace is
+    sized for ``max_active`` records of 17 levels unless ``pool_bytes`` sets
+    the pool explicitly.
     """
 
-    def __init__(self, integrator=BAOAB, precision=FP32, max_active=64, seed=1, stream=None):
+    def __init__(self, integrator=BAOAB, precision=FP32, max_active=64, seed=1, stream=None,
+                 pool_bytes=None):
         import torch
         self.integrator, self.precision = integrator, precision
-        nbytes = int(lib().mlmc_server_workspace_bytes(max_active))
+        if pool_bytes is None:
+            nbytes = int(lib().mlmc_server_workspace_bytes(max_active))
+        else:
+            nbytes = int(lib().mlmc_server_workspace_bytes(0)) + int(pool_bytes)
         self._buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         ptr = (self._buf.data_ptr() + 255) // 256 * 256
         self.stream = stream
@@ -657,6 +672,12 @@ class Server:
         _check(lib().mlmc_server_stats(self.handle, o), "mlmc_server_stats")
         return dict(ticks=int(o[0]), finished=int(o[1]), path_steps=o[2], busy_s=o[3],
                     active=int(o[4]), queued=int(o[5]))
+
+    def pool(self):
+        """(record bytes in use, pool bytes)."""
+        o = (C.c_uint64 * 2)()
+        _check(lib().mlmc_server_pool(self.handle, o), "mlmc_server_pool")
+        return int(o[0]), int(o[1])
 
     def run_until_idle(self, max_ticks=100000):
         for _ in range(max_ticks):

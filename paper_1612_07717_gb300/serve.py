@@ -38,6 +38,7 @@ def run(n=2000, rate_hz=200.0, seed=7, max_active=128, integrator=BAOAB, precisi
     ids = []
     t0 = time.perf_counter()
     k = 0
+    pool_peak = 0
     while k < n or srv.stats()["active"] + srv.stats()["queued"] > 0:
         now = time.perf_counter() - t0
         while k < n and queries[k][0] <= now:
@@ -45,6 +46,7 @@ def run(n=2000, rate_hz=200.0, seed=7, max_active=128, integrator=BAOAB, precisi
             ids.append(srv.submit(make_params(d, precision=precision), eps))
             k += 1
         srv.tick()
+        pool_peak = max(pool_peak, srv.pool()[0])
         if k < n and srv.stats()["active"] + srv.stats()["queued"] == 0:
             time.sleep(max(0.0, min(0.001, queries[k][0] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
@@ -55,10 +57,12 @@ def run(n=2000, rate_hz=200.0, seed=7, max_active=128, integrator=BAOAB, precisi
         steps += r["total_path_steps"]
         results.append(r)
     st = srv.stats()
+    srv_pool = srv.pool()[1]
     srv.close()
     lat = np.array(lat)
     return dict(queries=n, rate_hz=rate_hz, wall_s=wall, throughput_qps=n / wall,
                 path_steps_per_s=steps / wall, p50_ms=1e3 * float(np.percentile(lat, 50)),
                 p99_ms=1e3 * float(np.percentile(lat, 99)), mean_ms=1e3 * float(lat.mean()),
-                ticks=st["ticks"], max_active=max_active,
+                ticks=st["ticks"], max_active=max_active, pool_bytes=srv_pool,
+                pool_peak_bytes=pool_peak,
                 converged=int(sum(r["converged"] for r in results))), results, queries

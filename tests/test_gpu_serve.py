@@ -1,8 +1,11 @@
 """The continuous-batching query server (GPU): results are bitwise the same
 alone and in a mix of other queries, agree with the stand-alone adaptive
 estimator, every query finishes, a light query is not held up by heavy
-ones, launches keep their path-step budget, and served estimates agree with
-the FP64 oracle on a sampled subset."""
+ones, launches keep their path-step budget, queries are admitted by the
+device memory their records take (and results do not depend on how many
+fit at once), and served estimates agree with the FP64 oracle on a sampled
+subset.  Each query's per-level sums and driver live in its device record;
+the host only schedules."""
 import math
 
 import pytest
@@ -144,3 +147,40 @@ def test_fp64_server_and_extreme_slot_counts():
     big = G.Server(max_active=4096)                          # the largest slot table
     out = _drain(big, qs)
     assert [r["L"] for r in out] == [r["L"] for r in _drain(G.Server(max_active=2), qs)]
+
+
+def test_admission_is_by_memory():
+    qs = S.draw_queries(8, seed=5)
+    rec = G.server_query_bytes(G.make_params(qs[0][1]))
+    assert all(G.server_query_bytes(G.make_params(d)) == rec for _, d, _ in qs)
+    srv = G.Server(max_active=100, pool_bytes=2 * rec)   # room for two records
+    ids = [srv.submit(G.make_params(d), eps) for _, d, eps in qs]
+    peak = 0
+    while srv.stats()["active"] + srv.stats()["queued"] > 0:
+        srv.tick()
+        used, total = srv.pool()
+        assert used <= total == 2 * rec
+        assert srv.stats()["active"] <= 2
+        peak = max(peak, srv.stats()["active"])
+    assert peak == 2
+    assert srv.pool()[0] == 0                               # every record returned
+    ref = _drain(G.Server(max_active=8), qs)
+    for q, r in zip(ids, ref):
+        assert srv.poll(q)["estimate"] == r["estimate"]
+
+
+def test_records_grow_with_levels_and_oversized_queries_are_refused():
+    _, d, eps = S.draw_queries(1, seed=5)[0]
+    small = G.server_query_bytes(G.make_params(dict(d, L_max=6)))
+    big = G.server_query_bytes(G.make_params(dict(d, L_max=14)))
+    assert big > small > 0
+    srv = G.Server(max_active=100, pool_bytes=small)
+    with pytest.raises(G.MLMCError) as e:
+        srv.submit(G.make_params(dict(d, L_max=14)), eps)
+    assert e.value.code == G.EWORKSPACE
+    a = srv.submit(G.make_params(dict(d, L_max=6)), eps)
+    b = srv.submit(G.make_params(dict(d, L_max=6, stream_id=99)), eps)
+    srv.tick()
+    assert srv.stats()["active"] == 1 and srv.stats()["queued"] == 1   # one record fits
+    srv.run_until_idle()
+    assert srv.poll(a) is not None and srv.poll(b) is not None
