@@ -37,7 +37,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "1504956ebd9580d643acba66f0b49d8cf65f72bc", "bytes_per_launch": 0.945e6,
+TRAFFIC = {"kernel_sha1": "ee991fbd607a47b46c819f9c73c3b417a98225aa", "bytes_per_launch": 0.888e6,
            "fma_pipe_active_pct": 56.9, "fmaheavy_pipe_active_pct": 62.4,
            "issue_active_pct": 70.2, "thread_inst_per_path_step": 68.8}
 # The sources the persistent FP32 path kernels are compiled from.
