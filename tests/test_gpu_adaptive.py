@@ -216,3 +216,28 @@ def test_adaptive_empty_single_and_ragged(integ):
         assert s["n"] == o["n"] == n and s["path_steps"] == o["path_steps"]
         assert np.array_equal(np.array(s["sum"][1]), o["sum"][1])     # indicator counts
         assert np.allclose(s["sum"][0], o["sum"][0], rtol=1e-9, atol=1e-9 * n)
+
+
+@pytest.mark.parametrize("precision", [G.FP32, G.FP64])
+@pytest.mark.parametrize("case", [0, 2, 3, 4])
+def test_level_sums_are_the_sums_of_the_per_pair_outputs(case, precision):
+    # The level-sums kernel hands pairs out dynamically and parks their end
+    # states in shared memory; the per-pair output kernel runs one pair per
+    # thread.  The level sums must be the FP64 sums of the per-pair end
+    # states (counts and steps exactly), and the batched launch must agree.
+    integ, d, level = CASES[case]
+    N = 3001
+    pg = gpu_params(d, precision)
+    states, flags, steps = G.level_paths(level, N, integ, pg, 23, path_offset=11, steps=True)
+    gs, gf, gst = states.double().cpu().numpy(), flags.cpu().numpy(), steps.cpu().numpy()
+    s = G.level_sums(level, N, integ, pg, 23, path_offset=11)
+    ok = gf == 0
+    assert s["n"] == ok.sum() and s["n_nonfinite"] == (~ok).sum()
+    assert s["path_steps"] == int(gst.sum())
+    Y = gs[ok, 0] - gs[ok, 2]
+    for k, v in enumerate([Y.sum(), (Y * Y).sum(), gs[ok, 0].sum(), (gs[ok, 0] ** 2).sum(),
+                           gs[ok, 2].sum(), (gs[ok, 2] ** 2).sum()]):
+        assert s["sum"][0][k] == pytest.approx(v, rel=1e-12, abs=1e-9), k
+    b = G.multilevel_sums([(level, 11, N)], integ, pg, 23)[0]
+    assert b["n"] == s["n"] and b["path_steps"] == s["path_steps"]
+    assert np.allclose(b["sum"][0], s["sum"][0], rtol=1e-11)
