@@ -37,9 +37,9 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "ee991fbd607a47b46c819f9c73c3b417a98225aa", "bytes_per_launch": 0.888e6,
-           "fma_pipe_active_pct": 56.9, "fmaheavy_pipe_active_pct": 62.4,
-           "issue_active_pct": 70.2, "thread_inst_per_path_step": 68.8}
+TRAFFIC = {"kernel_sha1": "bd314c18d56d29f3af663117405e87743ed68af7", "bytes_per_launch": 0.977e6,
+           "fma_pipe_active_pct": 57.2, "fmaheavy_pipe_active_pct": 59.9,
+           "issue_active_pct": 72.3, "thread_inst_per_path_step": 70.3}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",

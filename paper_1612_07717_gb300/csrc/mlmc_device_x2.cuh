@@ -82,12 +82,14 @@ __device__ __forceinline__ void ou_factors_x2(float2 nsu, float2 nlam, float2 hl
   const float2 ny = mul2(nlam, hl2);
   e = make_float2(ptx_ex2(ny.x), ptx_ex2(ny.y));
   const float a = 2.0f * kLn2;
-  float2 s = f2(a * a * a * a * a / 120.0f);
-  s = fma2(s, ny, f2(a * a * a * a / 24.0f));
-  s = fma2(s, ny, f2(a * a * a / 6.0f));
-  s = fma2(s, ny, f2(a * a / 2.0f));
-  s = fma2(s, ny, f2(a));
-  const float2 nseries = mul2(s, ny);
+  // The series runs per lane on scalar FFMA, which the lighter FMA pipe can
+  // take: the packed ops keep the heavy FMA pipe busiest, and moving this
+  // chain off it was measured faster (0.8 %), while moving more was slower.
+  const float c5 = a * a * a * a * a / 120.0f, c4 = a * a * a * a / 24.0f;
+  const float c3 = a * a * a / 6.0f, c2 = a * a / 2.0f;
+  const float sx = fmaf(fmaf(fmaf(fmaf(c5, ny.x, c4), ny.x, c3), ny.x, c2), ny.x, a);
+  const float sy = fmaf(fmaf(fmaf(fmaf(c5, ny.y, c4), ny.y, c3), ny.y, c2), ny.y, a);
+  const float2 nseries = make_float2(sx * ny.x, sy * ny.y);
   const float2 ndirect = fma2(e, e, f2(-1.0f));
   const float2 nom = sel2(ny.x > -0.07f, ny.y > -0.07f, nseries, ndirect);
   c = mul2(nsu, mul2(nom, make_float2(ptx_rsqrt(-nom.x), ptx_rsqrt(-nom.y))));
