@@ -223,6 +223,25 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
                          const mlmc_params* p, uint64_t seed, void* workspace,
                          size_t ws_bytes, void* stream, mlmc_level_result* out);
 
+/* The work-item plan of a batched launch, for inspection and tests (host
+ * only: no device call, no GPU needed).  `grid` is the launch's block count
+ * (SMs x resident blocks per SM of the tuned variant); the tuning table
+ * gives the variant and the items per block.  For entry k of the launch
+ * order (finest level first, stable), out[5k .. 5k + 4] = {index of the
+ * request in reqs, paths per item, items, first item, single}.  Items hold
+ * whole passes of a block over its pairs: 256 pairs on a one-pair kernel,
+ * 512 on a packed one (two pairs per thread, variants 12 and 13), 256 again
+ * for a request the packed kernel runs one pair per thread (single = 1).
+ * A request goes single when one of its pairs alone is at least a quarter of
+ * a thread's average work (total path-steps / (grid * 256)): such pairs set
+ * the launch's length, and one pair per thread issues half the instructions
+ * per warp-step.  Either way every pair is the same bit for bit; only the
+ * FP64 rounding of the sums' grouping changes.  Errors as
+ * mlmc_multilevel_sums (MLMC_EINVAL for bad requests, grid < 1 or a batch
+ * that no split into at most 32768 items covers). */
+int mlmc_multilevel_plan(const mlmc_level_request* reqs, int n_req, int integrator,
+                         const mlmc_params* p, int grid, uint32_t* out);
+
 /* The batched launch of mlmc_multilevel_sums_async for callers that cannot
  * allocate device memory at all: a framework that owns every byte of device
  * memory through its own pool, a latency-bound loop that must never call

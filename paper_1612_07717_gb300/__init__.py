@@ -134,6 +134,8 @@ def lib():
         L.mlmc_estimate_pdf.argtypes = [C.c_double, i32, C.POINTER(Params), u64, i32, vp,
                                         C.c_size_t, vp, C.POINTER(C.c_double), C.POINTER(Result)]
         L.mlmc_stable_level_min.argtypes = [C.POINTER(Params), i32, C.POINTER(C.c_int32)]
+        L.mlmc_multilevel_plan.argtypes = [C.POINTER(LevelRequest), i32, i32, C.POINTER(Params),
+                                           i32, C.POINTER(C.c_uint32)]
         L.mlmc_set_tuning.argtypes = [i32, i32, i32, i32, i32]
         L.mlmc_get_tuning.argtypes = [i32, i32, C.POINTER(C.c_int32)]
         L.mlmc_server_workspace_bytes.restype = C.c_size_t
@@ -253,6 +255,22 @@ def multilevel_sums(requests, integrator, params, seed, workspace=None, stream=N
                                     _stream_handle(stream), out)
     _check(rc, "mlmc_multilevel_sums", allow=(ENONFINITE,))
     return [_level_result(out[k]) for k in range(n)]
+
+
+def multilevel_plan(requests, integrator, params, grid):
+    """Work-item plan of a batched launch on `grid` blocks (host only): one dict
+    per request in launch order (finest level first) with the request's index,
+    paths per item, items, first item and whether the packed kernel runs it one
+    pair per thread (``single``)."""
+    n = len(requests)
+    arr = (LevelRequest * n)()
+    for k, (lvl, first, count) in enumerate(requests):
+        arr[k].level, arr[k].first, arr[k].count = lvl, first, count
+    out = (C.c_uint32 * (5 * n))()
+    _check(lib().mlmc_multilevel_plan(arr, n, integrator, C.byref(params), grid, out),
+           "mlmc_multilevel_plan")
+    keys = ("request", "item_paths", "n_items", "item_base", "single")
+    return [dict(zip(keys, out[5 * k:5 * k + 5])) for k in range(n)]
 
 
 class MultilevelLaunch:

@@ -3,7 +3,8 @@
 For each (integrator, precision) it times the batched workload (all levels
 0..12 of the 600 m boundary layer, N_l = n0 * 10^(-l/2); n0 = 1e9 for FP32 by
 default, the benchmark's own size, since the best item size depends on the
-total work) for every combination of
+total work; SE, whose hierarchy starts at level 6, runs levels 6..12 scaled to
+the same path-steps) for every combination of
 
 * kernel variant: one path pair per thread, compiled for 1 (uncapped), 3 or
   4 resident 256-thread blocks per SM, or two pairs per thread on the packed
@@ -49,15 +50,38 @@ def get_tuning(integrator, precision):
     return dict(variant=out[0], items_per_block=out[1], blocks_per_sm=out[2])
 
 
+def _steps(sched, lm):
+    """Path-steps of a schedule: 8 * 2^l fine steps per pair, plus the coupled
+    coarse path's half as many above the base level."""
+    return sum(n * ((8 << l) * 3 // 2 if l > lm else (8 << l)) for l, n in sched)
+
+
+def tuning_schedule(integrator, n0):
+    """[(level, N_l)] of the tuned launch: levels level_min..12 of the BL600
+    hierarchy with N_l = n0 * 10^(-l/2).  A hierarchy that starts above level 0
+    (SE's stable base level) has its counts scaled up to the path-steps of the
+    levels-0..12 launch: cut to its finer levels alone, the launch would be so
+    short that the finest level's pairs -- tens of thousands of steps each,
+    sharing their warp scheduler with every other resident warp -- outlast the
+    rest of the work, and the sweep would rank how the work items happened to
+    land on the SMs rather than throughput."""
+    lm = W.bl600(integrator)["level_min"]
+    full = [(l, max(1, int(round(n * n0 / 1e9)))) for l, n in W.schedule_c4(levels=13, n0=1e9)]
+    sched = [(l, n) for l, n in full if l >= lm]
+    if lm > 0:
+        f = _steps(full, 0) / _steps(sched, lm)
+        sched = [(l, max(1, int(round(n * f)))) for l, n in sched]
+    return sched
+
+
 def _time_launch(integrator, precision, n0, reps=3):
     import torch
     d = W.bl600(integrator)
     lm = d["level_min"]
-    sched = [(l, max(1, int(round(n * n0 / 1e9)))) for l, n in W.schedule_c4(levels=13, n0=1e9)
-             if l >= lm]
+    sched = tuning_schedule(integrator, n0)
     p = make_params(d, precision=precision)
     launch = MultilevelLaunch([(l, 0, n) for l, n in sched], integrator, p, seed=1)
-    steps = sum(n * ((8 << l) * 3 // 2 if l > lm else (8 << l)) for l, n in sched)
+    steps = _steps(sched, lm)
     launch.run()
     torch.cuda.synchronize()
     best = float("inf")
@@ -106,8 +130,9 @@ def tune(integrators=(SE, GL, BAOAB), precisions=(FP32,), n0=1e9, verbose=False)
 
 def save(table, path=DEFAULT_FILE):
     doc = dict(gpu=gpu_name(), when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
-               workload="levels 0..12, N_l = n0 10^(-l/2), BL600 scenario, "
-               "n0 = 1e9 (FP32), 1e7 (FP64)", table=table)
+               workload="levels level_min..12, N_l = n0 10^(-l/2), BL600 scenario, "
+               "n0 = 1e9 (FP32), 1e7 (FP64); SE (level_min 6) scaled to the "
+               "path-steps of levels 0..12", table=table)
     with open(path, "w") as f:
         json.dump(doc, f, indent=1)
     return path

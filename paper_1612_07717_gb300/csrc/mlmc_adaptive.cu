@@ -177,7 +177,7 @@ cudaError_t multilevel(int integ, const HostModel& hm, const ReqPlan* plan, int 
     a.req[r].item_paths = plan[r].item_paths;
     a.req[r].n_items = plan[r].n_items;
     a.req[r].item_base = plan[r].item_base;
-    a.req[r].pad = 0;
+    a.req[r].single = 0;
   }
   a.n_req = n_req;
   a.n_items = n_items;
@@ -216,6 +216,29 @@ cudaError_t paths(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t 
   return cudaGetLastError();
 }
 
+// Resident blocks per SM of the adaptive multi-level kernel with its chunk's
+// dynamic shared memory (the attribute is raised first, as at launch).
+template <typename R>
+int multi_blocks_per_sm(int integ) {
+  const size_t smem = ChunkOf<R>::kBytes;
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (integ == kSE) {
+    cudaFuncSetAttribute(k_adapt_multilevel<kSE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adapt_multilevel<kSE, R>, kBlock,
+                                                      smem);
+  } else if (integ == kGL) {
+    cudaFuncSetAttribute(k_adapt_multilevel<kGL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adapt_multilevel<kGL, R>, kBlock,
+                                                      smem);
+  }
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  if (nb > kMaxBlocksPerSM) nb = kMaxBlocksPerSM;
+  return nb;
+}
+
 }  // namespace k_adapt
 
 cudaError_t launch_adapt_sums(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
@@ -232,6 +255,11 @@ cudaError_t launch_adapt_multilevel(int prec, int integ, const HostModel& hm, co
                                             grid, st)
               : k_adapt::multilevel<float>(integ, hm, plan, n_req, n_items, partials, counter,
                                            grid, st);
+}
+
+int adapt_multi_blocks_per_sm(int prec, int integ) {
+  return prec ? k_adapt::multi_blocks_per_sm<double>(integ)
+              : k_adapt::multi_blocks_per_sm<float>(integ);
 }
 
 cudaError_t launch_adapt_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,

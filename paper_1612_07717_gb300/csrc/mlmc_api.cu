@@ -72,9 +72,9 @@ MLMC_DECLARE_MULTI(prec_f32_x2b3)
 struct Tune {
   int variant, items_per_block, blocks_per_sm;
 };
-static Tune g_tune[3][2] = {{{1, 8, 0}, {1, 4, 0}},     // SE
-                            {{13, 16, 0}, {1, 16, 0}},  // GL
-                            {{13, 32, 0}, {1, 16, 0}}}; // BAOAB
+static Tune g_tune[3][2] = {{{12, 32, 0}, {1, 4, 0}},   // SE
+                            {{13, 32, 0}, {1, 4, 0}},   // GL
+                            {{13, 32, 0}, {1, 4, 0}}};  // BAOAB
 static std::mutex g_tune_mu;
 
 static Tune tune_of(int prec, int integ) {
@@ -517,6 +517,16 @@ int grid_for_variant(int variant, int prec, int integ) {
   return g;
 }
 
+// Grid of the adaptive multi-level kernel: its own occupancy (its chunk's
+// shared memory and registers), whatever uniform variant is tuned.
+static int grid_adapt_multi(int prec, int integ) {
+  DevInfo di;
+  if (device_info(&di) != MLMC_OK) return 0;
+  int g = di.sms * adapt_multi_blocks_per_sm(prec, integ);
+  if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
+  return g;
+}
+
 // Grid of the adaptive level-sums kernel: blocks take contiguous pair ranges,
 // sized from the one-pair level kernel's occupancy.
 static int grid_adapt(int prec, int integ, uint64_t N) {
@@ -710,13 +720,19 @@ int mlmc_level_sums(int level, uint64_t N, int integrator, const mlmc_params* p,
   return out->n_nonfinite ? MLMC_ENONFINITE : MLMC_OK;
 }
 
+// Work items per resident block of an adaptive launch (its pairs' costs vary,
+// so the tuned uniform kernel's item size does not carry over).
+static constexpr int kAdaptItemsPerBlock = 4;
+
 // Plan a multi-level launch: requests sorted by per-pair cost (finest level
 // first), split into items of about total / (items_per_block * grid)
 // path-steps, each a whole number of block passes over its pairs; the item
 // size doubles until the plan has at most max_items items.  Items are capped
 // at 2^31 - 1 pairs; a batch that still needs more than max_items items
-// returns too_many_rc.  Both batched forms (workspace and allocation-free)
-// plan with this function, so a batch that fits both gets the same items.
+// returns too_many_rc.  On a packed kernel, a request whose pairs are long
+// against a thread's share of the launch runs one pair per thread (single).
+// Both batched forms (workspace and allocation-free) plan with this
+// function, so a batch that fits both gets the same items.
 static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
                          const mlmc_params* p, int grid, uint32_t max_items, int too_many_rc,
                          ReqPlan* plan, int* order, uint32_t* n_items_out) {
@@ -737,10 +753,14 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
     order[j + 1] = v;
   }
   // about items_per_block items per resident block
-  double target = total / ((double)items_per_block(p->precision, integ) * (double)grid);
+  const int ipb = hm.adapt ? kAdaptItemsPerBlock : items_per_block(p->precision, integ);
+  double target = total / ((double)ipb * (double)grid);
   if (target < 1.0) target = 1.0;
   // the adaptive kernels run one pair per thread at a time
-  const uint64_t min_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
+  const uint64_t lane_paths = hm.adapt ? (uint64_t)kBlock : min_item_paths(p->precision, integ);
+  const bool packed = lane_paths > (uint64_t)kBlock;
+  // requests whose pairs are long against a thread's share run one pair per thread
+  const double single_steps = kSingleShare * total / ((double)grid * (double)kBlock);
   for (int pass = 0; pass < 64; ++pass) {
     uint64_t items = 0;
     bool capped = false;
@@ -748,6 +768,8 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       const mlmc_level_request& q = reqs[order[k]];
       LevelSpec ls;
       level_spec(hm, q.level, &ls);
+      const bool single = packed && (double)steps_per_pair(ls) >= single_steps;
+      const uint64_t min_paths = single ? (uint64_t)kBlock : lane_paths;
       double ppi = std::floor(target / (double)steps_per_pair(ls));
       uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
       item_paths -= item_paths % min_paths;   // whole passes of the block over its pairs
@@ -759,6 +781,7 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       plan[k].item_paths = (uint32_t)item_paths;
       plan[k].n_items = (uint32_t)n_it;
       plan[k].item_base = (uint32_t)items;
+      plan[k].single = single ? 1u : 0u;
       plan[k].path_steps = fixed_steps(hm, ls, q.count);
       items += n_it;
     }
@@ -783,7 +806,7 @@ static int multilevel_launch(const mlmc_level_request* reqs, int n_req, int inte
   Workspace w;
   if ((rc = carve(workspace, ws_bytes, &w))) return rc;
   const int prec = p->precision;
-  const int grid = grid_for(prec, integrator, true, 0);
+  const int grid = hm.adapt ? grid_adapt_multi(prec, integrator) : grid_for(prec, integrator, true, 0);
   if (grid <= 0) return MLMC_ENODEV;
   uint32_t n_items = 0;
   if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, (uint32_t)kMaxItems, MLMC_EINVAL,
@@ -795,6 +818,29 @@ static int multilevel_launch(const mlmc_level_request* reqs, int n_req, int inte
                                      w.counter, grid, st));
   if (rc) return rc;
   return cuda_status(launch_finalize_multi(w.partials, plan, n_req, d_sorted, st));
+}
+
+int mlmc_multilevel_plan(const mlmc_level_request* reqs, int n_req, int integrator,
+                         const mlmc_params* p, int grid, uint32_t* out) {
+  if (!out || !reqs || n_req < 1 || n_req > kMaxReq || grid < 1) return MLMC_EINVAL;
+  if (integrator < MLMC_SE || integrator > MLMC_BAOAB) return MLMC_EINVAL;
+  HostModel hm;
+  int rc = make_host_model(p, 0, &hm);
+  if (rc) return rc;
+  ReqPlan plan[kMaxReq];
+  int order[kMaxReq];
+  uint32_t n_items = 0;
+  if ((rc = plan_requests(hm, reqs, n_req, integrator, p, grid, (uint32_t)kMaxItems, MLMC_EINVAL,
+                          plan, order, &n_items)))
+    return rc;
+  for (int k = 0; k < n_req; ++k) {
+    out[5 * k + 0] = (uint32_t)order[k];
+    out[5 * k + 1] = plan[k].item_paths;
+    out[5 * k + 2] = plan[k].n_items;
+    out[5 * k + 3] = plan[k].item_base;
+    out[5 * k + 4] = plan[k].single;
+  }
+  return MLMC_OK;
 }
 
 int mlmc_multilevel_sums_async(const mlmc_level_request* reqs, int n_req, int integrator,
@@ -1309,7 +1355,7 @@ extern "C" int mlmc_multilevel_sums_noalloc(const mlmc_level_request* reqs, int 
   void* scratch = nullptr;
   if ((rc = noalloc_scratch(&scratch))) return rc;
   const int prec = p->precision;
-  const int grid = grid_for(prec, integrator, true, 0);
+  const int grid = hm.adapt ? grid_adapt_multi(prec, integrator) : grid_for(prec, integrator, true, 0);
   if (grid <= 0) return MLMC_ENODEV;
   // the workspace form's split (the requests are already finest level first,
   // so the plan's order is theirs); only a batch of more than kNoAllocItems

@@ -52,27 +52,33 @@ __device__ __forceinline__ uint64_t dev_steps(const GState* g, int l) {
 
 // Plan the levels with dN > 0, finest first, exactly as the host planner
 // does: items of about total / (items_per_block * grid) path-steps, in
-// whole passes of a block over its pairs (at least one).
+// whole passes of a block over its pairs (at least one); on a packed kernel,
+// levels whose pairs are long against a thread's share run one pair per thread.
 __device__ void plan_device(const GState* g, DevPlan* plan) {
   double total = 0.0;
   for (int l = g->L; l >= g->lmin; --l)
     if (g->dN[l]) total += (double)g->dN[l] * (double)dev_steps(g, l);
   double target = total / ((double)g->items_per_block * (double)g->grid);
   if (target < 1.0) target = 1.0;
+  const bool packed = g->min_item > kBlock;
+  const double single_steps = kSingleShare * total / ((double)g->grid * (double)kBlock);
   for (int pass = 0; pass < 40; ++pass) {
     uint64_t items = 0;
     int k = 0;
     for (int l = g->L; l >= g->lmin; --l) {
       if (!g->dN[l]) continue;
       const uint64_t spp = dev_steps(g, l);
+      const bool single = packed && (double)spp >= single_steps;
+      const uint64_t min_item = single ? (uint64_t)kBlock : (uint64_t)g->min_item;
       const double ppi = floor(target / (double)spp);
-      uint64_t item_paths = ppi < (double)g->min_item ? (uint64_t)g->min_item : (uint64_t)ppi;
-      item_paths -= item_paths % (uint64_t)g->min_item;
+      uint64_t item_paths = ppi < (double)min_item ? min_item : (uint64_t)ppi;
+      item_paths -= item_paths % min_item;
       if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
       const uint64_t n_it = (g->dN[l] + item_paths - 1) / item_paths;
       PlanReq& q = plan->req[k++];
       q.level = l;
       q.coupled = l > g->lmin;
+      q.single = single ? 1 : 0;
       q.M = (int64_t)g->M0 << l;
       q.h = g->T / (double)q.M;
       q.first = g->Ndone[l];

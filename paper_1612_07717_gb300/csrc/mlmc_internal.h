@@ -52,17 +52,25 @@ struct LevelSpec {
 };
 
 // One request of a multi-level launch after planning on the host.
+// A packed (two pairs per thread) launch runs a request one pair per thread
+// when one of its pairs alone is at least this share of a thread's average
+// work, total path-steps / (grid * kBlock): such pairs set the launch's
+// length, and one pair per thread issues half the instructions per warp-step.
+constexpr double kSingleShare = 0.25;
+
 struct ReqPlan {
   LevelSpec lv;
   uint64_t first, count;
   uint32_t item_paths, n_items, item_base;
+  uint32_t single;       // packed kernels: one pair per thread for this request's items
   uint64_t path_steps;
 };
 
 // A request of a device-planned multi-level launch (the graph-driven
 // estimator plans on the device), precision independent, 64 bytes.
 struct PlanReq {
-  int32_t level, coupled;
+  int32_t level;
+  uint16_t coupled, single;   // single: packed kernels run the items one pair per thread
   int64_t M;
   double h;
   uint64_t first, count, path_steps;
@@ -104,6 +112,8 @@ cudaError_t launch_adapt_sums(int prec, int integ, const HostModel& hm, const Le
 cudaError_t launch_adapt_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                                     int n_req, uint32_t n_items, Partial* partials,
                                     unsigned int* counter, int grid, cudaStream_t st);
+// Resident blocks per SM of the adaptive multi-level kernel.
+int adapt_multi_blocks_per_sm(int prec, int integ);
 cudaError_t launch_adapt_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                                uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
                                int64_t* d_steps, cudaStream_t st);

@@ -310,7 +310,7 @@ template <typename R>
 struct ReqDev {
   Level<R> lv;
   uint64_t first, count;
-  uint32_t item_paths, n_items, item_base, pad;
+  uint32_t item_paths, n_items, item_base, single;
 };
 
 template <typename R>
@@ -324,14 +324,23 @@ struct MultiArgs {
 };
 
 
+// `single` (packed kernels only) runs the item one pair per thread on the
+// scalar path: the launch's longest pairs then take half the warps' issue
+// slots per step, which shortens a launch whose finest level outlasts the
+// rest of the work.  Both paths give the same pairs bit for bit.
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
-                                                uint64_t first, uint32_t count, Acc& acc) {
+                                                uint64_t first, uint32_t count, bool single,
+                                                Acc& acc) {
   if constexpr (MLMC_X2 && std::is_same<R, float>::value) {
 #if MLMC_X2
-    multilevel_item_x2<INTEG, COUPLED>(m, lv, first, count, acc);
+    if (!single) {
+      multilevel_item_x2<INTEG, COUPLED>(m, lv, first, count, acc);
+      return;
+    }
 #endif
-  } else {
+  }
+  {
     for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
       Path<R> f, c;
       bool bad;
@@ -363,9 +372,9 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel(const __grid_c
     acc_zero(acc, a.m.qoi1_mode != 0);
     const Level<R> lv = rq.lv;   // registers, not parameter-space loads per step
     if (lv.coupled)
-      multilevel_item<INTEG, R, true>(a.m, lv, rq.first + start, count, acc);
+      multilevel_item<INTEG, R, true>(a.m, lv, rq.first + start, count, rq.single != 0, acc);
     else
-      multilevel_item<INTEG, R, false>(a.m, lv, rq.first + start, count, acc);
+      multilevel_item<INTEG, R, false>(a.m, lv, rq.first + start, count, rq.single != 0, acc);
     block_reduce_store(acc, lv.coupled != 0, a.m.qoi1_mode != 0, a.partials + it);
   }
 }
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
     rq.first = pr.first;
     rq.count = pr.count;
     rq.item_paths = pr.item_paths;
-    rq.pad = 0;
+    rq.single = pr.single;
     const uint32_t local = it - pr.item_base;
     const uint64_t start = (uint64_t)local * pr.item_paths;
     const uint64_t left = pr.count - start;
@@ -410,9 +419,9 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB) k_multilevel_dev(const __gr
     Acc acc;
     acc_zero(acc, m.qoi1_mode != 0);
     if (pr.coupled)
-      multilevel_item<INTEG, R, true>(m, rq.lv, pr.first + start, count, acc);
+      multilevel_item<INTEG, R, true>(m, rq.lv, pr.first + start, count, pr.single != 0, acc);
     else
-      multilevel_item<INTEG, R, false>(m, rq.lv, pr.first + start, count, acc);
+      multilevel_item<INTEG, R, false>(m, rq.lv, pr.first + start, count, pr.single != 0, acc);
     block_reduce_store(acc, pr.coupled != 0, m.qoi1_mode != 0, partials + it);
   }
 }
@@ -464,9 +473,9 @@ __global__ void __launch_bounds__(kBlock, MLMC_MINB)
     Acc acc;
     acc_zero(acc, m.qoi1_mode != 0);
     if (pr.coupled)
-      multilevel_item<INTEG, R, true>(m, lv, pr.first + start, count, acc);
+      multilevel_item<INTEG, R, true>(m, lv, pr.first + start, count, pr.single != 0, acc);
     else
-      multilevel_item<INTEG, R, false>(m, lv, pr.first + start, count, acc);
+      multilevel_item<INTEG, R, false>(m, lv, pr.first + start, count, pr.single != 0, acc);
     block_reduce_store(acc, pr.coupled != 0, m.qoi1_mode != 0, partials + it);
   }
 }
@@ -699,7 +708,7 @@ cudaError_t multilevel_impl(int integ, const HostModel& hm, const ReqPlan* plan,
     a.req[r].item_paths = plan[r].item_paths;
     a.req[r].n_items = plan[r].n_items;
     a.req[r].item_base = plan[r].item_base;
-    a.req[r].pad = 0;
+    a.req[r].single = plan[r].single;
   }
   a.n_req = n_req;
   a.n_items = n_items;

@@ -280,6 +280,7 @@ static PlanReq chunk_request(const Query& q, int l, uint64_t first, uint64_t cou
   PlanReq r;
   r.level = l;
   r.coupled = l > q.p.level_min;
+  r.single = 0;
   r.M = (int64_t)q.p.M0 << l;
   r.h = q.p.T / (double)r.M;
   r.first = first;

@@ -37,6 +37,7 @@ def mlmc_cost(eps, integ, seed=1, z_adapt=0.0, n_init=4000, L_max=12, precision=
     p = make_params(d, precision=precision)
     ws = Workspace(p)
     run = estimate if z_adapt > 0 else estimate_graph
+    run(eps, integ, p, seed + 1000, workspace=ws)   # warm-up: module loading, first graph
     t = time.perf_counter()
     r = run(eps, integ, p, seed, workspace=ws)
     dt = time.perf_counter() - t
@@ -47,8 +48,10 @@ def mlmc_cost(eps, integ, seed=1, z_adapt=0.0, n_init=4000, L_max=12, precision=
 
 def stmc_cost(eps, integ, level, seed=2, n_pilot=4000, precision=FP32):
     p = make_params(dict(W.PAPER, level_min=level), precision=precision)
+    ws = Workspace(p)
+    stmc_estimate(eps, level, integ, p, seed + 1000, n_pilot=n_pilot, workspace=ws)  # warm-up
     t = time.perf_counter()
-    s = stmc_estimate(eps, level, integ, p, seed, n_pilot=n_pilot, workspace=Workspace(p))
+    s = stmc_estimate(eps, level, integ, p, seed, n_pilot=n_pilot, workspace=ws)
     dt = time.perf_counter() - t
     return dict(level=level, h=W.PAPER["T"] / (W.PAPER["M0"] << level), N=s["N"][0],
                 estimate=s["estimate"][0], path_steps=s["total_path_steps"], seconds=dt)

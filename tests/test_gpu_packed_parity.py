@@ -117,24 +117,33 @@ def test_all_variants_give_the_same_pairs_bit_for_bit(integ, precision):
 
 
 @pytest.mark.parametrize("variant", PACKED)
-def test_packed_batched_sums_are_the_sums_of_its_pairs(variant):
-    d = W.bl600(G.BAOAB)
+@pytest.mark.parametrize("integ", INTEGS)
+def test_packed_batched_sums_are_the_sums_of_its_pairs(integ, variant):
+    # a few long pairs beside many short ones: the plan runs the finest
+    # request one pair per thread (its pairs are long against a thread's
+    # share of the launch) and the coarsest two per thread; either way the
+    # sums are the FP64 sums of the pairs the variant's own lanes compute
+    d = W.bl600(integ)
+    lm = d["level_min"]
     p = gpu_params(d)
-    saved = autotune.get_tuning(G.BAOAB, G.FP32)
-    reqs = [(5, 3, 20001), (2, 0, 100001), (0, 7, 300001)]
+    saved = autotune.get_tuning(integ, G.FP32)
+    reqs = [(lm + 6, 3, 3001), (lm + 1, 0, 200001), (lm, 7, 1000003)]
     try:
-        autotune.set_tuning(G.BAOAB, G.FP32, variant, 32, 0)
-        got = G.multilevel_sums(reqs, G.BAOAB, p, 13)
+        autotune.set_tuning(integ, G.FP32, variant, 32, 0)
+        grid = G.device_info()["sms"] * {12: 2, 13: 3}[variant]
+        plan = G.multilevel_plan(reqs, integ, p, grid)
+        assert [e["single"] for e in plan] == [1, 0, 0]
+        got = G.multilevel_sums(reqs, integ, p, 13)
         for (level, first, count), g in zip(reqs, got):
-            s, f = G.level_paths(level, count, G.BAOAB, p, 13, path_offset=first,
+            s, f = G.level_paths(level, count, integ, p, 13, path_offset=first,
                                  variant=variant)
             ref = sums_from_states(s.double().cpu().numpy(), f.cpu().numpy(),
-                                   d["qoi_threshold"], level > d["level_min"], G.FP32)
+                                   d["qoi_threshold"], level > lm, G.FP32)
             assert g["n"] == ref["n"] and g["n_nonfinite"] == ref["n_nonfinite"]
             assert np.array_equal(np.array(g["sum"][1]), ref["sum"][1])
             assert np.allclose(g["sum"][0], ref["sum"][0], rtol=1e-11, atol=1e-9)
     finally:
-        autotune.set_tuning(G.BAOAB, G.FP32, saved["variant"], saved["items_per_block"],
+        autotune.set_tuning(integ, G.FP32, saved["variant"], saved["items_per_block"],
                             saved["blocks_per_sm"])
 
 
