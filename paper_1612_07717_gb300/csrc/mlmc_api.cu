@@ -189,7 +189,10 @@ int blocks_per_sm(int prec, int integ, bool multilevel) {
 // ---------------------------------------------------------------------------
 // Fixed-order reductions of block / item partials into mlmc_level_result.
 // One block per result; thread t takes partials t, t + 256, ... with Kahan
-// compensation, then the same warp tree and warp-ordered Kahan sum.
+// compensation, then the same warp tree and warp-ordered Kahan sum, one lane
+// of warp 0 per sum (FP64 instructions hold the FP64 pipe for many cycles
+// whatever the number of active lanes, so the sums go side by side).  A warp
+// none of whose threads took a partial skips its tree: its sums are zeros.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kadd(double& s, double& c, double x) {
   const double y = x - c;
@@ -214,31 +217,32 @@ __device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint
   }
   double v[12];
   for (int k = 0; k < 12; ++k) v[k] = s[k] - c[k];
-  for (int off = 16; off > 0; off >>= 1) {
-    for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-    for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (begin + (uint32_t)(warp * 32) < end) {
+    for (int off = 16; off > 0; off >>= 1) {
+      for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+      for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    }
+  }
   if (lane == 0) {
     for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
     for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[12], tc[12];
-    for (int k = 0; k < 12; ++k) t[k] = tc[k] = 0.0;
-    unsigned long long q[3] = {0, 0, 0};
-    for (int w = 0; w < kBlock / 32; ++w) {
-      for (int k = 0; k < 12; ++k) kadd(t[k], tc[k], s_v[w][k]);
-      for (int k = 0; k < 3; ++k) q[k] += s_u[w][k];
-    }
-    out->n = q[0];
-    out->n_nonfinite = q[1];
-    // fixed step counts come from the host; 0 selects the counted steps
-    out->path_steps = path_steps ? path_steps : q[2];
+  if (threadIdx.x < 12) {
+    const int k = threadIdx.x;
+    double t = 0.0, tc = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) kadd(t, tc, s_v[w][k]);
+    out->sum[k / 6][k % 6] = t - tc;
+  } else if (threadIdx.x < 15) {
+    const int k = threadIdx.x - 12;
+    unsigned long long q = 0;
+    for (int w = 0; w < kBlock / 32; ++w) q += s_u[w][k];
+    if (k == 0) out->n = q;
+    else if (k == 1) out->n_nonfinite = q;
+    else out->path_steps = path_steps ? path_steps : q;  // fixed counts come from the host
+  } else if (threadIdx.x == 15) {
     out->reserved = 0;
-    for (int k = 0; k < 6; ++k) out->sum[0][k] = t[k] - tc[k];
-    for (int k = 0; k < 6; ++k) out->sum[1][k] = t[6 + k] - tc[6 + k];
   }
 }
 

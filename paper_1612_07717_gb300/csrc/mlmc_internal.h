@@ -11,6 +11,7 @@ namespace mlmc {
 constexpr int kBlock = 256;          // threads per block of every path kernel
 constexpr int kMaxReq = 32;          // requests in one multi-level launch
 constexpr int kMaxItems = 32768;     // work items in one multi-level launch
+constexpr int kMaxPdfBins = 32;      // bins of the binned density
 constexpr int kMaxBlocksPerSM = 8;   // 2048 threads / kBlock
 
 // Partial sums of one thread block (or one work item), 128 bytes: for each

@@ -168,8 +168,12 @@ __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, b
   a.n += 1;
 }
 
-// Warp tree (fixed order), then lane 0 of warp 0 adds the warp results in
-// warp order with Kahan compensation.  Ends with the block synchronised.
+// Warp tree (fixed order), then the warp results are added in warp order with
+// Kahan compensation, one lane of warp 0 per sum.  FP64 instructions hold the
+// FP64 pipe for many cycles whatever the number of active lanes, so the sums
+// go side by side in the lanes rather than one after another in one thread; a
+// warp whose lanes saw no pair skips its tree (its sums are exact zeros).
+// Ends with the block synchronised.
 __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, bool smooth,
                                                    Partial* __restrict__ out) {
   __shared__ double s_v[kBlock / 32][12];
@@ -184,14 +188,16 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
     v[6] = nf - nc; v[7] = nd; v[8] = nf; v[9] = nf; v[10] = nc; v[11] = nc;
   }
   unsigned long long u[3] = {a.n, a.bad, a.steps};
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (__any_sync(0xFFFFFFFFu, a.n + a.bad != 0)) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
+    }
+  }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
@@ -199,19 +205,17 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
     for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s[12], c[12];
-    for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
-    unsigned long long t[3] = {0, 0, 0};
-    for (int w = 0; w < kBlock / 32; ++w) {
-      for (int k = 0; k < 12; ++k) kahan_add(s[k], c[k], s_v[w][k]);
-      for (int k = 0; k < 3; ++k) t[k] += s_u[w][k];
-    }
-    for (int k = 0; k < 6; ++k) out->s0[k] = s[k] - c[k];
-    for (int k = 0; k < 6; ++k) out->s1[k] = s[6 + k] - c[6 + k];
-    out->n = t[0];
-    out->bad = t[1];
-    out->steps = t[2];
+  if (threadIdx.x < 12) {
+    const int k = threadIdx.x;
+    double s = 0.0, c = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, c, s_v[w][k]);
+    (k < 6 ? out->s0 : out->s1)[k < 6 ? k : k - 6] = s - c;
+  } else if (threadIdx.x < 15) {
+    const int k = threadIdx.x - 12;
+    unsigned long long t = 0;
+    for (int w = 0; w < kBlock / 32; ++w) t += s_u[w][k];
+    (k == 0 ? out->n : k == 1 ? out->bad : out->steps) = t;
+  } else if (threadIdx.x == 15) {
     out->pad = 0;
   }
   __syncthreads();
@@ -525,21 +529,21 @@ __global__ void __launch_bounds__(kBlock) k_level_pdf(const __grid_constant__ Pd
       gc0 = gc1;
     }
   }
-  // block reduction of each column: warp tree, then warp-ordered Kahan
-  __shared__ double s_w[kBlock / 32];
+  // block reduction of each column: warp tree, then warp-ordered Kahan, one
+  // thread per column (side by side: FP64 instructions are slow to issue)
+  __shared__ double s_w[kBlock / 32][2 * kMaxPdfBins + 2];
   const int lane = t & 31, warp = t >> 5;
   double* out = a.partials + (size_t)blockIdx.x * (2 * k + 2);
   for (int col = 0; col < 2 * k + 2; ++col) {
     double v = col < 2 * k ? s_pdf[col * kBlock + t] : (col == 2 * k ? n_ok : n_bad);
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
-    if (lane == 0) s_w[warp] = v;
-    __syncthreads();
-    if (t == 0) {
-      double s = 0.0, cc = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, cc, s_w[w]);
-      out[col] = s - cc;
-    }
-    __syncthreads();
+    if (lane == 0) s_w[warp][col] = v;
+  }
+  __syncthreads();
+  for (int col = t; col < 2 * k + 2; col += kBlock) {
+    double s = 0.0, cc = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, cc, s_w[w][col]);
+    out[col] = s - cc;
   }
 }
 

@@ -11,7 +11,6 @@
 
 namespace mlmc {
 
-constexpr int kMaxBins = 32;
 
 // Column sums of the per-block pdf partials, in block order (Kahan).
 __global__ void __launch_bounds__(kBlock) k_finalize_pdf(const double* __restrict__ p, int nblocks,
@@ -65,7 +64,7 @@ extern "C" {
 int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params* p, uint64_t seed,
                         uint64_t path_offset, int k, void* workspace, size_t ws_bytes,
                         void* stream, double* out, uint64_t* n_ok, uint64_t* n_nonfinite) {
-  if (!out || !n_ok || !n_nonfinite || k < 1 || k > kMaxBins) return MLMC_EINVAL;
+  if (!out || !n_ok || !n_nonfinite || k < 1 || k > kMaxPdfBins) return MLMC_EINVAL;
   if (integrator < MLMC_SE || integrator > MLMC_BAOAB || !p || !(p->smooth_delta > 0.0))
     return MLMC_EINVAL;
   HostModel hm;
@@ -88,7 +87,7 @@ int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params
   if (rc) return rc;
   k_finalize_pdf<<<ncols, kBlock, 0, st>>>(partials, grid, ncols, res);
   if ((rc = cuda_status(cudaGetLastError()))) return rc;
-  double host[2 * kMaxBins + 2];
+  double host[2 * kMaxPdfBins + 2];
   rc = cuda_status(cudaMemcpyAsync(host, res, ncols * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
   if (rc) return rc;
@@ -107,7 +106,7 @@ int mlmc_level_pdf_sums(int level, uint64_t N, int integrator, const mlmc_params
 int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t seed, int k,
                       void* workspace, size_t ws_bytes, void* stream, double* pdf,
                       mlmc_result* out) {
-  if (!out || !pdf || !p || !(eps > 0.0) || k < 1 || k > kMaxBins) return MLMC_EINVAL;
+  if (!out || !pdf || !p || !(eps > 0.0) || k < 1 || k > kMaxPdfBins) return MLMC_EINVAL;
   if (p->L_max < p->level_min + 2 || p->L_max >= MLMC_MAX_LEVELS || p->n_init < 2)
     return MLMC_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
@@ -128,7 +127,7 @@ int mlmc_estimate_pdf(double eps, int integrator, const mlmc_params* p, uint64_t
     for (int pass = 0; pass < 2; ++pass) {
       for (int l = lmin; l <= L; ++l) {
         if (!dN[l]) continue;
-        double sums[2 * kMaxBins];
+        double sums[2 * kMaxPdfBins];
         uint64_t nok = 0, nbad = 0;
         int rc = mlmc_level_pdf_sums(l, dN[l], integrator, p, seed, Ndone[l], k, workspace,
                                      ws_bytes, stream, sums, &nok, &nbad);
