@@ -44,6 +44,7 @@ struct GraphRegion {
   mlmc_result result;
 };
 static_assert(sizeof(GraphRegion) <= kGraphRegion, "graph region");
+static_assert(sizeof(GState) % 8 == 0 && sizeof(mlmc_result) % 8 == 0, "zeroed in 8-byte words");
 
 __device__ __forceinline__ uint64_t dev_steps(const GState* g, int l) {
   const int64_t M = (int64_t)g->M0 << l;
@@ -97,39 +98,64 @@ __device__ void plan_device(const GState* g, DevPlan* plan) {
   }
 }
 
-__device__ void write_result(const GState* g, mlmc_result* out) {
-  memset(out, 0, sizeof(*out));
-  out->L = g->L;
-  out->converged = g->converged;
-  for (int q = 0; q < 2; ++q) {
-    double est = 0.0, var = 0.0;
-    for (int l = g->lmin; l <= g->L; ++l) {
-      const double n = (double)g->n[l];
-      const double m1 = g->S[l][q][0], m2 = g->S[l][q][1];
-      est += m1 / n;
-      const double v = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
-      var += (v > 0.0 ? v : 0.0) / n;
-    }
-    out->estimate[q] = est;
-    out->est_variance[q] = var;
-  }
-  for (int l = g->lmin; l <= g->L; ++l) {
+// Zero `bytes` (a multiple of 8) at an 8-byte aligned address, one warp.
+__device__ void warp_zero(void* p, size_t bytes, int lane) {
+  unsigned long long* q = (unsigned long long*)p;
+  for (size_t i = lane; i < bytes / 8; i += 32) q[i] = 0ull;
+  __syncwarp();
+}
+
+// The result of the loop, by one warp: the per-level terms one lane per
+// level, their sums over levels in level order on lane 0.
+__device__ void write_result(const GState* g, mlmc_result* out, int lane) {
+  __shared__ double s_est[2][kLevels], s_var[2][kLevels];
+  const int nl = g->L - g->lmin + 1;
+  for (int i = lane; i < nl; i += 32) {
+    const int l = g->lmin + i;
     const double n = (double)g->n[l];
-    out->N[l] = g->n[l];
+    for (int q = 0; q < 2; ++q) {
+      const double m1 = g->S[l][q][0], m2 = g->S[l][q][1];
+      s_est[q][i] = m1 / n;
+      const double v = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
+      s_var[q][i] = (v > 0.0 ? v : 0.0) / n;
+    }
+  }
+  warp_zero(out, sizeof(*out), lane);
+  if (lane == 0) {
+    out->L = g->L;
+    out->converged = g->converged;
+    for (int q = 0; q < 2; ++q) {
+      double est = 0.0, var = 0.0;
+      for (int i = 0; i < nl; ++i) {
+        est += s_est[q][i];
+        var += s_var[q][i];
+      }
+      out->estimate[q] = est;
+      out->est_variance[q] = var;
+    }
+    for (int l = g->lmin; l <= g->L; ++l) {
+      out->N[l] = g->n[l];
+      out->total_path_steps += g->steps[l];
+      out->n_nonfinite += g->bad[l];
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < nl; i += 32) {
+    const int l = g->lmin + i;
+    const double n = (double)g->n[l];
     out->mean_y[l] = g->S[l][0][0] / n;
     const double v = n > 1.0 ? (g->S[l][0][1] - g->S[l][0][0] * g->S[l][0][0] / n) / (n - 1.0) : 0.0;
     out->V[l] = v > 0.0 ? v : 0.0;
-    out->total_path_steps += g->steps[l];
-    out->n_nonfinite += g->bad[l];
   }
 }
 
 __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, int Lmax, int n_init,
                              int M0, int grid, int ipb, int min_item, int max_iter, double eps,
                              double T) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   GState* g = &r->g;
-  memset(g, 0, sizeof(*g));
+  warp_zero(g, sizeof(*g), threadIdx.x);              // the warp clears the state
+  if (threadIdx.x != 0) return;
   g->lmin = lmin;
   g->Lmax = Lmax;
   g->n_init = n_init;
@@ -147,69 +173,95 @@ __global__ void k_graph_init(GraphRegion* r, unsigned int* counter, int lmin, in
   *counter = 0;
 }
 
-// One driver pass after a launch (single thread; a few hundred flops).
+// One driver pass after a launch, by one warp.  FP64 instructions are slow
+// to issue on this GPU, so the per-request folds and the per-level sample
+// sizes go one lane each; sums over levels run in level order, so every
+// value is the one a single thread computing level by level gets.
 __global__ void k_graph_update(GraphRegion* r, const mlmc_level_result* __restrict__ res,
                                unsigned int* counter, cudaGraphConditionalHandle handle) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
   GState* g = &r->g;
   const DevPlan* plan = &r->plan;
-  for (int k = 0; k < plan->n_req; ++k) {            // fold in the sums just computed
+  const int n_req = plan->n_req;
+  for (int idx = lane; idx < 12 * n_req; idx += 32) {   // fold in the sums just computed
+    const int k = idx / 12, j = idx % 12;
+    const int l = plan->req[k].level;                  // each level once per plan
+    g->S[l][j / 6][j % 6] += res[k].sum[j / 6][j % 6];
+  }
+  for (int k = lane; k < n_req; k += 32) {
     const int l = plan->req[k].level;
-    for (int q = 0; q < 2; ++q)
-      for (int j = 0; j < 6; ++j) g->S[l][q][j] += res[k].sum[q][j];
     g->n[l] += res[k].n;
     g->bad[l] += res[k].n_nonfinite;
     g->steps[l] += res[k].path_steps;
     g->Ndone[l] += plan->req[k].count;
     g->dN[l] = 0;
   }
-  g->iter += 1;
+  __syncwarp();
+  __shared__ double s_vc[kLevels];
   bool more = false;
   if (g->pass == 0) {                                // step 3: optimal N_l
-    double V[kLevels], C[kLevels], total = 0.0;
-    for (int l = g->lmin; l <= g->L; ++l) {
+    const int nl = g->L - g->lmin + 1;
+    double V[(kLevels + 31) / 32], C[(kLevels + 31) / 32];
+    for (int i = lane, m = 0; i < nl; i += 32, ++m) {
+      const int l = g->lmin + i;
       const double n = (double)g->n[l];
       const double m1 = g->S[l][0][0], m2 = g->S[l][0][1];
-      V[l] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
-      if (V[l] < 0.0) V[l] = 0.0;
-      C[l] = (double)dev_steps(g, l);
-      total += sqrt(V[l] * C[l]);
+      V[m] = n > 1.0 ? (m2 - m1 * m1 / n) / (n - 1.0) : 0.0;
+      if (V[m] < 0.0) V[m] = 0.0;
+      C[m] = (double)dev_steps(g, l);
+      s_vc[i] = sqrt(V[m] * C[m]);
     }
-    for (int l = g->lmin; l <= g->L; ++l) {
-      const double Nopt = ceil(2.0 / (g->eps * g->eps) * sqrt(V[l] / C[l]) * total);
+    __syncwarp();
+    double total = 0.0;
+    for (int i = 0; i < nl; ++i) total += s_vc[i];
+    bool due = false;
+    for (int i = lane, m = 0; i < nl; i += 32, ++m) {
+      const int l = g->lmin + i;
+      const double Nopt = ceil(2.0 / (g->eps * g->eps) * sqrt(V[m] / C[m]) * total);
       g->dN[l] = Nopt > (double)g->Ndone[l] ? (uint64_t)(Nopt - (double)g->Ndone[l]) : 0;
-      more |= g->dN[l] != 0;
+      due |= g->dN[l] != 0;
     }
-    g->pass = 1;                                     // step 4 runs next if anything is due
+    more = __any_sync(0xFFFFFFFFu, due);
+    __syncwarp();
+    if (lane == 0) g->pass = 1;                      // step 4 runs next if anything is due
+    __syncwarp();
   }
-  if (!more) {                                       // step 5: bias test
-    bool conv = false;
-    if (g->L >= g->lmin + 2) {
-      const double yL = fabs(g->S[g->L][0][0] / (double)g->n[g->L]);
-      const double yL1 = fabs(g->S[g->L - 1][0][0] / (double)g->n[g->L - 1]);
-      conv = fmax(yL1 / 2.0, yL) < g->eps / sqrt(2.0);
+  if (lane == 0) {
+    g->iter += 1;
+    if (!more) {                                     // step 5: bias test
+      bool conv = false;
+      if (g->L >= g->lmin + 2) {
+        const double yL = fabs(g->S[g->L][0][0] / (double)g->n[g->L]);
+        const double yL1 = fabs(g->S[g->L - 1][0][0] / (double)g->n[g->L - 1]);
+        conv = fmax(yL1 / 2.0, yL) < g->eps / sqrt(2.0);
+      }
+      if (conv || g->L >= g->Lmax) {
+        g->converged = conv ? 1 : 0;
+      } else {                                       // step 6: add a level
+        g->L += 1;
+        g->dN[g->L] = (uint64_t)g->n_init;
+        g->pass = 0;
+        more = true;
+      }
     }
-    if (conv || g->L >= g->Lmax) {
-      g->converged = conv ? 1 : 0;
-    } else {                                         // step 6: add a level
-      g->L += 1;
-      g->dN[g->L] = (uint64_t)g->n_init;
-      g->pass = 0;
-      more = true;
+    if (more && g->iter >= g->max_iter) {            // the loop's watchdog
+      g->status = MLMC_ETIMEOUT;
+      more = false;
     }
+    if (more) {
+      plan_device(g, &r->plan);
+    } else {
+      g->done = 1;
+    }
+    *counter = 0;
+    cudaGraphSetConditional(handle, more ? 1u : 0u);
   }
-  if (more && g->iter >= g->max_iter) {       // the loop's watchdog
-    g->status = MLMC_ETIMEOUT;
-    more = false;
+  more = __shfl_sync(0xFFFFFFFFu, more, 0);
+  if (!more) {
+    __syncwarp();
+    write_result(g, &r->result, lane);
   }
-  if (more) {
-    plan_device(g, &r->plan);
-  } else {
-    g->done = 1;
-    write_result(g, &r->result);
-  }
-  *counter = 0;
-  cudaGraphSetConditional(handle, more ? 1u : 0u);
 }
 
 }  // namespace mlmc
