@@ -45,6 +45,7 @@ KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
                   "paper_1612_07717_gb300/csrc/mlmc_device_x2.cuh",
                   "paper_1612_07717_gb300/csrc/mlmc_kernels.cuh",
+                  "paper_1612_07717_gb300/csrc/mlmc_reduce.cuh",
                   "paper_1612_07717_gb300/csrc/mlmc_kernels_inst.inc",
                   "paper_1612_07717_gb300/csrc/mlmc_kernels_f32.cu",
                   "paper_1612_07717_gb300/csrc/mlmc_kernels_f32_b3.cu",

@@ -9,6 +9,7 @@
 #include <utility>
 
 #include "mlmc_internal.h"
+#include "mlmc_reduce.cuh"
 
 // NVTX ranges name the host-side phases in a profiler's timeline (a no-op
 // unless a tool is attached).
@@ -203,7 +204,7 @@ __device__ __forceinline__ void kadd(double& s, double& c, double x) {
 
 __device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint32_t end,
                              uint64_t path_steps, mlmc_level_result* __restrict__ out) {
-  __shared__ double s_v[kBlock / 32][12];
+  __shared__ double s_tree[kBlock / 32][12][16];
   __shared__ unsigned long long s_u[kBlock / 32][3];
   double s[12], c[12];
   for (int k = 0; k < 12; ++k) s[k] = c[k] = 0.0;
@@ -219,20 +220,19 @@ __device__ void reduce_range(const Partial* __restrict__ p, uint32_t begin, uint
   for (int k = 0; k < 12; ++k) v[k] = s[k] - c[k];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (begin + (uint32_t)(warp * 32) < end) {
-    for (int off = 16; off > 0; off >>= 1) {
-      for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+    warp_tree12(v, s_tree[warp], lane);
+    for (int off = 16; off > 0; off >>= 1)
       for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
-    }
+  } else if (lane < 12) {
+    s_tree[warp][lane][0] = 0.0;
   }
-  if (lane == 0) {
-    for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
+  if (lane == 0)
     for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
-  }
   __syncthreads();
   if (threadIdx.x < 12) {
     const int k = threadIdx.x;
     double t = 0.0, tc = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) kadd(t, tc, s_v[w][k]);
+    for (int w = 0; w < kBlock / 32; ++w) kadd(t, tc, s_tree[w][k][0]);
     out->sum[k / 6][k % 6] = t - tc;
   } else if (threadIdx.x < 15) {
     const int k = threadIdx.x - 12;

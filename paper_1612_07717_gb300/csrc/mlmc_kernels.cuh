@@ -15,6 +15,7 @@
 
 #include "mlmc_device.cuh"
 #include "mlmc_internal.h"
+#include "mlmc_reduce.cuh"
 #if MLMC_X2
 #include "mlmc_device_x2.cuh"
 #endif
@@ -168,15 +169,17 @@ __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, b
   a.n += 1;
 }
 
-// Warp tree (fixed order), then the warp results are added in warp order with
-// Kahan compensation, one lane of warp 0 per sum.  FP64 instructions hold the
-// FP64 pipe for many cycles whatever the number of active lanes, so the sums
-// go side by side in the lanes rather than one after another in one thread; a
-// warp whose lanes saw no pair skips its tree (its sums are exact zeros).
-// Ends with the block synchronised.
+// Warp tree (fixed order, warp_tree12), then the warp results are added in
+// warp order with Kahan compensation, one lane of warp 0 per sum.  FP64
+// instructions hold the FP64 pipe for many cycles whatever the number of
+// active lanes, so the sums go side by side in the lanes rather than one after
+// another in one thread; a warp whose lanes saw no pair skips its tree (its
+// sums are exact zeros).  Ends with the block synchronised.
 __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, bool smooth,
                                                    Partial* __restrict__ out) {
-  __shared__ double s_v[kBlock / 32][12];
+  // the warp trees reuse the smoothed QoI's per-thread sums (12 KB, read above)
+  double (*s_tree)[12][16] = reinterpret_cast<double (*)[12][16]>(&q1_smem()[0][0]);
+  static_assert(sizeof(double) * 6 * kBlock == sizeof(double) * (kBlock / 32) * 12 * 16, "tree buffer");
   __shared__ unsigned long long s_u[kBlock / 32][3];
   double v[12] = {a.y, a.y2, coupled ? a.pf : a.y, coupled ? a.pf2 : a.y2, a.pc, a.pc2};
   if (smooth) {
@@ -189,18 +192,18 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
   }
   unsigned long long u[3] = {a.n, a.bad, a.steps};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();                       // every thread has read its smoothed sums
   if (__any_sync(0xFFFFFFFFu, a.n + a.bad != 0)) {
+    warp_tree12(v, s_tree[warp], lane);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-#pragma unroll
       for (int k = 0; k < 3; ++k) u[k] += __shfl_down_sync(0xFFFFFFFFu, u[k], off);
     }
+  } else if (lane < 12) {
+    s_tree[warp][lane][0] = 0.0;
   }
   if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) s_v[warp][k] = v[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) s_u[warp][k] = u[k];
   }
@@ -208,7 +211,7 @@ __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, b
   if (threadIdx.x < 12) {
     const int k = threadIdx.x;
     double s = 0.0, c = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, c, s_v[w][k]);
+    for (int w = 0; w < kBlock / 32; ++w) kahan_add(s, c, s_tree[w][k][0]);
     (k < 6 ? out->s0 : out->s1)[k < 6 ? k : k - 6] = s - c;
   } else if (threadIdx.x < 15) {
     const int k = threadIdx.x - 12;

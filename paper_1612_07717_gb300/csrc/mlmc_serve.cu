@@ -165,7 +165,9 @@ __device__ void qdriver(QView& v) {
 
 __device__ void qresult(const QView& v, mlmc_result* out) {
   const QHead* h = v.h;
-  memset(out, 0, sizeof(*out));
+  // cleared in 8-byte words (one thread: a byte-wise memset is many times slower)
+  static_assert(sizeof(mlmc_result) % 8 == 0, "result in 8-byte words");
+  for (size_t k = 0; k < sizeof(mlmc_result) / 8; ++k) ((unsigned long long*)out)[k] = 0ull;
   out->L = h->L;
   out->converged = h->converged;
   for (int k = 0; k < 2; ++k) {
