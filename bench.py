@@ -37,9 +37,9 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "49b8b4cf18486a377a5aaee6c7bafd93f093415e", "bytes_per_launch": 0.890e6,
-           "fma_pipe_active_pct": 57.1, "fmaheavy_pipe_active_pct": 61.1,
-           "issue_active_pct": 72.0, "thread_inst_per_path_step": 70.4}
+TRAFFIC = {"kernel_sha1": "df3a81766337c3fa038f392e5598c442f0aed08d", "bytes_per_launch": 0.798e6,
+           "fma_pipe_active_pct": 57.2, "fmaheavy_pipe_active_pct": 61.2,
+           "issue_active_pct": 72.0, "thread_inst_per_path_step": 69.8}
 # The sources the persistent FP32 path kernels are compiled from.
 KERNEL_SOURCES = ("include/mlmc.h", "paper_1612_07717_gb300/csrc/mlmc_internal.h",
                   "paper_1612_07717_gb300/csrc/mlmc_device.cuh",
