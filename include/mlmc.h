@@ -234,9 +234,9 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
  * for a request the packed kernel runs one pair per thread (single = 1).
  * A request goes single when one of its pairs alone is at least a quarter of
  * a thread's average work (total path-steps / (grid * 256)): such pairs set
- * the launch's length, and one pair per thread issues half the instructions
- * per warp-step.  Either way every pair is the same bit for bit; only the
- * FP64 rounding of the sums' grouping changes.  Errors as
+ * the launch's length, and one pair per thread needs about two thirds of a
+ * packed warp's instructions per step.  Either way every pair is the same
+ * bit for bit; only the FP64 rounding of the sums' grouping changes.  Errors as
  * mlmc_multilevel_sums (MLMC_EINVAL for bad requests, grid < 1 or a batch
  * that no split into at most 32768 items covers). */
 int mlmc_multilevel_plan(const mlmc_level_request* reqs, int n_req, int integrator,

@@ -56,7 +56,8 @@ struct LevelSpec {
 // A packed (two pairs per thread) launch runs a request one pair per thread
 // when one of its pairs alone is at least this share of a thread's average
 // work, total path-steps / (grid * kBlock): such pairs set the launch's
-// length, and one pair per thread issues half the instructions per warp-step.
+// length, and one pair per thread issues about two thirds of a packed warp's
+// instructions per step.
 constexpr double kSingleShare = 0.25;
 
 struct ReqPlan {

@@ -177,7 +177,8 @@ __device__ __forceinline__ void acc_add(Acc& a, const Model<R>& m, R zf, R zc, b
 // sums are exact zeros).  Ends with the block synchronised.
 __device__ __forceinline__ void block_reduce_store(const Acc& a, bool coupled, bool smooth,
                                                    Partial* __restrict__ out) {
-  // the warp trees reuse the smoothed QoI's per-thread sums (12 KB, read above)
+  // the warp trees reuse the smoothed QoI's per-thread sums (12 KB), each
+  // thread reading its own sums into v before the barrier below
   double (*s_tree)[12][16] = reinterpret_cast<double (*)[12][16]>(&q1_smem()[0][0]);
   static_assert(sizeof(double) * 6 * kBlock == sizeof(double) * (kBlock / 32) * 12 * 16, "tree buffer");
   __shared__ unsigned long long s_u[kBlock / 32][3];
@@ -332,9 +333,10 @@ struct MultiArgs {
 
 
 // `single` (packed kernels only) runs the item one pair per thread on the
-// scalar path: the launch's longest pairs then take half the warps' issue
-// slots per step, which shortens a launch whose finest level outlasts the
-// rest of the work.  Both paths give the same pairs bit for bit.
+// scalar path: a warp of the launch's longest pairs then issues about two
+// thirds of the instructions per step, which shortens a launch whose finest
+// level outlasts the rest of the work.  Both paths give the same pairs bit for
+// bit.
 template <int INTEG, typename R, bool COUPLED>
 __device__ __forceinline__ void multilevel_item(const Model<R>& m, const Level<R> lv,
                                                 uint64_t first, uint32_t count, bool single,
