@@ -37,7 +37,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "df3a81766337c3fa038f392e5598c442f0aed08d", "bytes_per_launch": 0.798e6,
+TRAFFIC = {"kernel_sha1": "0599b847719e9d8626b7a26353511bd8e4ae8854", "bytes_per_launch": 0.798e6,
            "fma_pipe_active_pct": 57.2, "fmaheavy_pipe_active_pct": 61.2,
            "issue_active_pct": 72.0, "thread_inst_per_path_step": 69.8}
 # The sources the persistent FP32 path kernels are compiled from.
@@ -63,8 +63,9 @@ def kernel_sha1():
     token = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\s+', re.S)
 
     def code(text):
-        return token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else
-                         ("" if m.group(0)[0] in "/" else " "), text)
+        # comments out first, then every whitespace run (comment lines included) to one space
+        text = token.sub(lambda m: "" if m.group(0)[0] == "/" else m.group(0), text)
+        return token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
     h = hashlib.sha1()
     for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, name), encoding="utf-8") as f:
