@@ -216,6 +216,30 @@ cudaError_t paths(int integ, const HostModel& hm, const LevelSpec& ls, uint64_t 
   return cudaGetLastError();
 }
 
+// Resident blocks per SM of the adaptive level-sums kernel (coupled form)
+// with its chunk's dynamic shared memory (the attribute is raised first, as
+// at launch).
+template <typename R>
+int sums_blocks_per_sm(int integ) {
+  const size_t smem = ChunkOf<R>::kBytes;
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (integ == kSE) {
+    cudaFuncSetAttribute(k_adapt_sums<kSE, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adapt_sums<kSE, R, true>, kBlock,
+                                                      smem);
+  } else if (integ == kGL) {
+    cudaFuncSetAttribute(k_adapt_sums<kGL, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adapt_sums<kGL, R, true>, kBlock,
+                                                      smem);
+  }
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  if (nb > kMaxBlocksPerSM) nb = kMaxBlocksPerSM;
+  return nb;
+}
+
 // Resident blocks per SM of the adaptive multi-level kernel with its chunk's
 // dynamic shared memory (the attribute is raised first, as at launch).
 template <typename R>
@@ -255,6 +279,11 @@ cudaError_t launch_adapt_multilevel(int prec, int integ, const HostModel& hm, co
                                             grid, st)
               : k_adapt::multilevel<float>(integ, hm, plan, n_req, n_items, partials, counter,
                                            grid, st);
+}
+
+int adapt_sums_blocks_per_sm(int prec, int integ) {
+  return prec ? k_adapt::sums_blocks_per_sm<double>(integ)
+              : k_adapt::sums_blocks_per_sm<float>(integ);
 }
 
 int adapt_multi_blocks_per_sm(int prec, int integ) {

@@ -532,11 +532,11 @@ static int grid_adapt_multi(int prec, int integ) {
 }
 
 // Grid of the adaptive level-sums kernel: blocks take contiguous pair ranges,
-// sized from the one-pair level kernel's occupancy.
+// as many blocks as the kernel keeps resident (its own registers and chunk).
 static int grid_adapt(int prec, int integ, uint64_t N) {
   DevInfo di;
   if (device_info(&di) != MLMC_OK) return 0;
-  int g = di.sms * (prec ? prec_f64::occupancy(integ, false) : prec_f32::occupancy(integ, false));
+  int g = di.sms * adapt_sums_blocks_per_sm(prec, integ);
   if ((size_t)g > kMaxGridBlocks) g = (int)kMaxGridBlocks;
   const uint64_t need = (N + kBlock - 1) / kBlock;
   if (need < (uint64_t)g) g = (int)(need > 0 ? need : 1);

@@ -114,7 +114,8 @@ cudaError_t launch_adapt_sums(int prec, int integ, const HostModel& hm, const Le
 cudaError_t launch_adapt_multilevel(int prec, int integ, const HostModel& hm, const ReqPlan* plan,
                                     int n_req, uint32_t n_items, Partial* partials,
                                     unsigned int* counter, int grid, cudaStream_t st);
-// Resident blocks per SM of the adaptive multi-level kernel.
+// Resident blocks per SM of the adaptive level-sums and multi-level kernels.
+int adapt_sums_blocks_per_sm(int prec, int integ);
 int adapt_multi_blocks_per_sm(int prec, int integ);
 cudaError_t launch_adapt_paths(int prec, int integ, const HostModel& hm, const LevelSpec& lv,
                                uint64_t N, uint64_t offset, void* d_states, int32_t* d_flags,
