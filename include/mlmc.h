@@ -226,7 +226,9 @@ int mlmc_multilevel_sums(const mlmc_level_request* reqs, int n_req, int integrat
 /* The work-item plan of a batched launch, for inspection and tests (host
  * only: no device call, no GPU needed).  `grid` is the launch's block count
  * (SMs x resident blocks per SM of the tuned variant); the tuning table
- * gives the variant and the items per block.  For entry k of the launch
+ * gives the variant and the items per block (a batch with adaptive
+ * timesteps runs its own kernel: one pair per thread, 4 items per block,
+ * whatever the table says).  For entry k of the launch
  * order (finest level first, stable), out[5k .. 5k + 4] = {index of the
  * request in reqs, paths per item, items, first item, single}.  Items hold
  * whole passes of a block over its pairs: 256 pairs on a one-pair kernel,
