@@ -360,7 +360,8 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
  * smaller one) a pass that would start another one ends the loop instead,
  * and mlmc_graph_result returns MLMC_ETIMEOUT with the partial result.
  *   mlmc_graph_create   builds and instantiates the graph (host work; no
- *                       kernel runs yet); returns an opaque handle
+ *                       kernel runs yet; two pinned host buffers, about
+ *                       5 KB, receive the result); returns an opaque handle
  *   mlmc_graph_launch   enqueues one complete estimate on `stream`
  *   mlmc_graph_result   copies the result of the last launch into *out and
  *                       synchronises `stream`; same codes as mlmc_estimate

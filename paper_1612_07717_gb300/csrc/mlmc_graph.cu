@@ -6,6 +6,7 @@
 // the sample-size rule and the bias test, plans the next launch and sets the
 // loop condition; the host only launches the graph and reads the result.
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -27,7 +28,8 @@ namespace mlmc {
 constexpr int kLevels = MLMC_MAX_LEVELS;
 constexpr int kMaxIterations = 4 * kLevels;  // default pass limit: more than a converging run takes
 
-// Driver state in the workspace's graph region.
+// Driver state in the workspace's graph region.  The host reads back the
+// leading int32 block only (kGStateHead bytes: done and status).
 struct GState {
   int32_t L, pass, iter, converged, status, lmin, Lmax, n_init;
   int32_t M0, grid, done, items_per_block;
@@ -44,6 +46,7 @@ struct GraphRegion {
   mlmc_result result;
 };
 static_assert(sizeof(GraphRegion) <= kGraphRegion, "graph region");
+constexpr size_t kGStateHead = offsetof(GState, eps);
 static_assert(sizeof(GState) % 8 == 0 && sizeof(mlmc_result) % 8 == 0, "zeroed in 8-byte words");
 
 __device__ __forceinline__ uint64_t dev_steps(const GState* g, int l) {
@@ -275,6 +278,10 @@ struct mlmc_graph_s {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GraphRegion* region = nullptr;
   int lmin = 0;
+  // pinned host copies of the result and of the state's leading fields
+  // (a pageable copy goes through a staging buffer and takes longer)
+  mlmc_result* h_result = nullptr;
+  GState* h_head = nullptr;
 };
 
 static void graph_free(mlmc_graph_s* g) {
@@ -284,6 +291,8 @@ static void graph_free(mlmc_graph_s* g) {
   if (g->cap) cudaStreamDestroy(g->cap);
   if (g->e0) cudaEventDestroy(g->e0);
   if (g->e1) cudaEventDestroy(g->e1);
+  if (g->h_result) cudaFreeHost(g->h_result);
+  if (g->h_head) cudaFreeHost(g->h_head);
   delete g;
 }
 
@@ -332,6 +341,8 @@ int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint6
   CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
   CK(cudaEventCreate(&g->e0));
   CK(cudaEventCreate(&g->e1));
+  CK(cudaHostAlloc((void**)&g->h_result, sizeof(mlmc_result), cudaHostAllocDefault));
+  CK(cudaHostAlloc((void**)&g->h_head, sizeof(GState), cudaHostAllocDefault));
   CK(cudaGraphCreate(&g->graph, 0));
   // init kernel
   CK(cudaStreamBeginCaptureToGraph(g->cap, g->graph, nullptr, nullptr, 0,
@@ -384,12 +395,14 @@ int mlmc_graph_launch(mlmc_graph g, void* stream) {
 int mlmc_graph_result(mlmc_graph g, void* stream, mlmc_result* out) {
   if (!g || !out) return MLMC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  GState gs;
-  if (cudaMemcpyAsync(out, &g->region->result, sizeof(*out), cudaMemcpyDeviceToHost, st) !=
+  if (cudaMemcpyAsync(g->h_result, &g->region->result, sizeof(mlmc_result),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(g->h_head, &g->region->g, kGStateHead, cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
-      cudaMemcpyAsync(&gs, &g->region->g, sizeof(gs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MLMC_ECUDA;
+  *out = *g->h_result;
+  const GState& gs = *g->h_head;
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, g->e0, g->e1) == cudaSuccess) out->seconds = 1e-3 * ms;
   if (!gs.done) return MLMC_ECUDA;
