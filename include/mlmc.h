@@ -361,12 +361,14 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
  * and mlmc_graph_result returns MLMC_ETIMEOUT with the partial result.
  *   mlmc_graph_create   builds and instantiates the graph (host work; no
  *                       kernel runs yet; two pinned host buffers, about
- *                       5 KB, receive the result); returns an opaque handle
+ *                       5 KB, receive the result of each launch); returns
+ *                       an opaque handle
  *   mlmc_graph_launch   enqueues one complete estimate on `stream`
  *   mlmc_graph_result   copies the result of the last launch into *out and
  *                       synchronises `stream`; same codes as mlmc_estimate
  *   mlmc_graph_destroy  frees the handle (host resources only)
- * mlmc_estimate_graph does all four once.  The graph's estimate equals
+ * mlmc_estimate_graph does all four once (without the pinned buffers, whose
+ * allocation would cost more than they save on a single launch).  The graph's estimate equals
  * mlmc_estimate's up to the FP64 rounding of the level sums (the batched
  * kernel groups paths into items differently). */
 typedef struct mlmc_graph_s* mlmc_graph;

@@ -278,8 +278,9 @@ struct mlmc_graph_s {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GraphRegion* region = nullptr;
   int lmin = 0;
-  // pinned host copies of the result and of the state's leading fields
-  // (a pageable copy goes through a staging buffer and takes longer)
+  // pinned host copies of the result and of the state's leading fields, for
+  // graphs launched many times (a pageable copy goes through a staging
+  // buffer and takes longer; a one-shot estimate skips the allocation)
   mlmc_result* h_result = nullptr;
   GState* h_head = nullptr;
 };
@@ -298,8 +299,9 @@ static void graph_free(mlmc_graph_s* g) {
 
 extern "C" {
 
-int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint64_t seed,
-                         int max_passes, void* workspace, size_t ws_bytes, mlmc_graph* out) {
+static int graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                        int max_passes, void* workspace, size_t ws_bytes, bool pinned,
+                        mlmc_graph* out) {
   if (!out || !p || !(eps > 0.0)) return MLMC_EINVAL;
   *out = nullptr;
   if (max_passes < 0 || max_passes > kMaxIterations) return MLMC_EINVAL;
@@ -341,8 +343,15 @@ int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint6
   CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
   CK(cudaEventCreate(&g->e0));
   CK(cudaEventCreate(&g->e1));
-  CK(cudaHostAlloc((void**)&g->h_result, sizeof(mlmc_result), cudaHostAllocDefault));
-  CK(cudaHostAlloc((void**)&g->h_head, sizeof(GState), cudaHostAllocDefault));
+  if (pinned) {
+    CK(cudaHostAlloc((void**)&g->h_result, sizeof(mlmc_result), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&g->h_head, sizeof(GState), cudaHostAllocDefault));
+    // one copy into each now, so that the first launch's read-back is not the first use
+    CK(cudaMemcpyAsync(g->h_result, &g->region->result, sizeof(mlmc_result),
+                       cudaMemcpyDeviceToHost, g->cap));
+    CK(cudaMemcpyAsync(g->h_head, &g->region->g, kGStateHead, cudaMemcpyDeviceToHost, g->cap));
+    CK(cudaStreamSynchronize(g->cap));
+  }
   CK(cudaGraphCreate(&g->graph, 0));
   // init kernel
   CK(cudaStreamBeginCaptureToGraph(g->cap, g->graph, nullptr, nullptr, 0,
@@ -377,9 +386,14 @@ int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint6
   return MLMC_OK;
 }
 
+int mlmc_graph_create_ex(double eps, int integrator, const mlmc_params* p, uint64_t seed,
+                         int max_passes, void* workspace, size_t ws_bytes, mlmc_graph* out) {
+  return graph_create(eps, integrator, p, seed, max_passes, workspace, ws_bytes, true, out);
+}
+
 int mlmc_graph_create(double eps, int integrator, const mlmc_params* p, uint64_t seed,
                       void* workspace, size_t ws_bytes, mlmc_graph* out) {
-  return mlmc_graph_create_ex(eps, integrator, p, seed, 0, workspace, ws_bytes, out);
+  return graph_create(eps, integrator, p, seed, 0, workspace, ws_bytes, true, out);
 }
 
 int mlmc_graph_launch(mlmc_graph g, void* stream) {
@@ -395,14 +409,17 @@ int mlmc_graph_launch(mlmc_graph g, void* stream) {
 int mlmc_graph_result(mlmc_graph g, void* stream, mlmc_result* out) {
   if (!g || !out) return MLMC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(g->h_result, &g->region->result, sizeof(mlmc_result),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(g->h_head, &g->region->g, kGStateHead, cudaMemcpyDeviceToHost, st) !=
+  GState head;
+  mlmc_result* res = g->h_result ? g->h_result : out;
+  GState* hd = g->h_head ? g->h_head : &head;
+  if (cudaMemcpyAsync(res, &g->region->result, sizeof(mlmc_result), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(hd, &g->region->g, kGStateHead, cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MLMC_ECUDA;
-  *out = *g->h_result;
-  const GState& gs = *g->h_head;
+  if (res != out) *out = *res;
+  const GState& gs = *hd;
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, g->e0, g->e1) == cudaSuccess) out->seconds = 1e-3 * ms;
   if (!gs.done) return MLMC_ECUDA;
@@ -420,7 +437,7 @@ int mlmc_estimate_graph(double eps, int integrator, const mlmc_params* p, uint64
                         void* workspace, size_t ws_bytes, void* stream, mlmc_result* out) {
   if (!out) return MLMC_EINVAL;
   mlmc_graph g = nullptr;
-  int rc = mlmc_graph_create(eps, integrator, p, seed, workspace, ws_bytes, &g);
+  int rc = graph_create(eps, integrator, p, seed, 0, workspace, ws_bytes, false, &g);
   if (rc) return rc;
   const auto t0 = std::chrono::steady_clock::now();
   rc = mlmc_graph_launch(g, stream);
