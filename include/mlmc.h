@@ -351,7 +351,7 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
 /* The same adaptive estimate with the whole loop on the device, as one CUDA
  * graph: an init kernel, then a conditional while-node whose body is the
  * persistent multi-level kernel over the levels that need samples, the
- * fixed-order per-level reduction, and a one-thread update kernel that adds
+ * fixed-order per-level reduction, and a one-warp update kernel that adds
  * the sums, applies N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)),
  * the bias test and the next plan, and sets the loop condition.  The driver
  * state, plan and result live in the workspace (which must stay alive and
@@ -368,7 +368,8 @@ int mlmc_estimate_result(const mlmc_estimate_state* st, const mlmc_params* p, ml
  *                       synchronises `stream`; same codes as mlmc_estimate
  *   mlmc_graph_destroy  frees the handle (host resources only)
  * mlmc_estimate_graph does all four once (without the pinned buffers, whose
- * allocation would cost more than they save on a single launch).  The graph's estimate equals
+ * allocation would cost more than they save on a single launch).  The
+ * graph's estimate equals
  * mlmc_estimate's up to the FP64 rounding of the level sums (the batched
  * kernel groups paths into items differently). */
 typedef struct mlmc_graph_s* mlmc_graph;
