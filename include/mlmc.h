@@ -257,7 +257,7 @@ int mlmc_multilevel_plan(const mlmc_level_request* reqs, int n_req, int integrat
  * split into the same items as mlmc_multilevel_sums_async uses whenever that
  * split has at most 4096 items (the sums are then bit-identical); a larger
  * split gets larger items until it fits; a batch that cannot be split that
- * way (more than 4096 * (2^31 - 1) pairs) returns MLMC_EWORKSPACE, more than
+ * way (more than about 4096 * 2^31 pairs) returns MLMC_EWORKSPACE, more than
  * 32 requests MLMC_EINVAL.  It calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *

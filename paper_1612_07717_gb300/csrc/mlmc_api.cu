@@ -732,9 +732,10 @@ static constexpr int kAdaptItemsPerBlock = 4;
 // first), split into items of about total / (items_per_block * grid)
 // path-steps, each a whole number of block passes over its pairs; the item
 // size doubles until the plan has at most max_items items.  Items are capped
-// at 2^31 - 1 pairs; a batch that still needs more than max_items items
-// returns too_many_rc.  On a packed kernel, a request whose pairs are long
-// against a thread's share of the launch runs one pair per thread (single).
+// below 2^31 pairs (in whole passes); a batch that still needs more than
+// max_items items returns too_many_rc.  On a packed kernel, a request whose
+// pairs are long against a thread's share of the launch runs one pair per
+// thread (single).
 // Both batched forms (workspace and allocation-free) plan with this
 // function, so a batch that fits both gets the same items.
 static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, int n_req, int integ,
@@ -777,7 +778,10 @@ static int plan_requests(const HostModel& hm, const mlmc_level_request* reqs, in
       double ppi = std::floor(target / (double)steps_per_pair(ls));
       uint64_t item_paths = ppi < (double)min_paths ? min_paths : (uint64_t)ppi;
       item_paths -= item_paths % min_paths;   // whole passes of the block over its pairs
-      if (item_paths > 0x7FFFFFFFull) { item_paths = 0x7FFFFFFFull; capped = true; }
+      if (item_paths > 0x7FFFFFFFull) {   // at most 2^31 - 1 pairs, in whole passes
+        item_paths = 0x7FFFFFFFull - 0x7FFFFFFFull % min_paths;
+        capped = true;
+      }
       const uint64_t n_it = q.count ? (q.count + item_paths - 1) / item_paths : 0;
       plan[k].lv = ls;
       plan[k].first = q.first;

@@ -77,7 +77,7 @@ __device__ void plan_device(const GState* g, DevPlan* plan) {
       const double ppi = floor(target / (double)spp);
       uint64_t item_paths = ppi < (double)min_item ? min_item : (uint64_t)ppi;
       item_paths -= item_paths % min_item;
-      if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
+      if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull - 0x7FFFFFFFull % min_item;
       const uint64_t n_it = (g->dN[l] + item_paths - 1) / item_paths;
       PlanReq& q = plan->req[k++];
       q.level = l;

@@ -278,7 +278,7 @@ static PlanReq chunk_request(const Query& q, int l, uint64_t first, uint64_t cou
   const uint64_t min_paths = (count + kMaxItemsPerReq - 1) / kMaxItemsPerReq;
   if (item_paths < min_paths) item_paths = min_paths;
   item_paths += (min_item - item_paths % min_item) % min_item;  // whole passes of the block
-  if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull;
+  if (item_paths > 0x7FFFFFFFull) item_paths = 0x7FFFFFFFull - 0x7FFFFFFFull % min_item;
   PlanReq r;
   r.level = l;
   r.coupled = l > q.p.level_min;

@@ -140,3 +140,20 @@ def test_adaptive_plan_does_not_follow_the_uniform_kernels_tuning(tuning, integ)
         plans.append(G.multilevel_plan(reqs, integ, pa, 304))
     assert plans[0] == plans[1] == plans[2]
     _check_cover(reqs, plans[0], dict(W.PAPER), packed=False)
+
+
+def test_huge_batches_cap_items_below_2_31_pairs_in_whole_passes(tuning):
+    # 2^45 pairs need items larger than 2^31 - 1 pairs: they are capped at the
+    # largest whole number of block passes below that and still cover the batch;
+    # at 2^46 pairs even capped items exceed the 32768 items of one launch
+    tuning(G.GL, G.FP32, 13, 32, 0)
+    d = W.bl600(G.GL)
+    p = G.make_params(d)
+    reqs = [(0, 0, 2 ** 45)]
+    plan = G.multilevel_plan(reqs, G.GL, p, 456)
+    assert plan[0]["item_paths"] <= 2 ** 31 - 1
+    assert plan[0]["item_paths"] >= 2 ** 31 - 2 * BLOCK
+    _check_cover(reqs, plan, d, packed=True)
+    with pytest.raises(G.MLMCError) as e:
+        G.multilevel_plan([(0, 0, 2 ** 46)], G.GL, p, 456)
+    assert e.value.code == G.EINVAL
