@@ -37,7 +37,7 @@ FLOPS_PER_PATH_STEP = 181.0 / 3.0
 # (launch list), the FMA-pipe, heavy-FMA-pipe and issue-slot activity of the
 # full-size launch (one-pass metric captures) and, from the full capture of the
 # 1e8-path case, the thread instructions per path-step.
-TRAFFIC = {"kernel_sha1": "0599b847719e9d8626b7a26353511bd8e4ae8854", "bytes_per_launch": 0.798e6,
+TRAFFIC = {"kernel_sha1": "bbff457a9eab73fdc81666ad40f83962b3732fda", "bytes_per_launch": 0.945e6,
            "fma_pipe_active_pct": 57.2, "fmaheavy_pipe_active_pct": 61.2,
            "issue_active_pct": 72.0, "thread_inst_per_path_step": 69.8}
 # The sources the persistent FP32 path kernels are compiled from.
